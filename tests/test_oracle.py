@@ -1,0 +1,297 @@
+"""Pins for the CPU oracle: it is checked against things other than itself.
+
+* hand-worked fixtures (tests/golden) -- exact fractions from the definitions;
+* exact integer / dyadic products L U and L L^t, which the elimination must
+  recover bit for bit (every intermediate is a short dyadic number);
+* Cramer's rule in exact rationals for n <= 4;
+* invariants: P A = L U within the GEPP rounding bound, |l_ij| <= 1;
+* special cases with known answers (identity, permutation, singular, non-SPD);
+* CPU LAPACK (torch.linalg) as an independent cross-check of pivots and factors.
+"""
+import itertools
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1511_07174_gb300 import inputs
+from tests.golden.reader import load
+
+U64 = 2.0 ** -53
+
+
+def _np(t):
+    return np.asfortranarray(t.numpy())
+
+
+# ----------------------------------------------------------------- golden files
+def test_golden_gepp_4x4():
+    g = load("gepp_4x4.txt")
+    A = np.array(g["A"], dtype=np.float64)
+    LU, ipiv, info = oracle.getrf(A)
+    assert info == 0
+    assert list(ipiv) == [int(v) for v in g["ipiv"]]
+    L, U = oracle.unpack_lu(LU)
+    Lx = np.array([[float(v) for v in r] for r in g["L"]])
+    Ux = np.array([[float(v) for v in r] for r in g["U"]])
+    assert np.abs(L - Lx).max() <= 4 * U64 * 1.0
+    assert np.abs(U - Ux).max() <= 4 * U64 * 17.0
+    x = oracle.getrs(LU, ipiv, np.array([float(v) for v in g["b"]]))
+    assert np.abs(x[:, 0] - 1.0).max() <= 64 * U64
+
+
+def test_golden_chol_3x3():
+    g = load("chol_3x3.txt")
+    A = np.array(g["A"], dtype=np.float64)
+    L, info = oracle.potrf(A)
+    assert info == 0
+    Lx = np.array([[float(v) for v in r] for r in g["L"]])
+    assert np.array_equal(np.tril(L), Lx)
+    assert np.array_equal(np.triu(L, 1), np.triu(A, 1))   # upper untouched
+
+
+# ----------------------------------------------------------- exact recoveries
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 16, 33, 64, 150])
+def test_dyadic_lu_exact(n):
+    A, L0, U0, perm = inputs.dyadic_lu(n, seed=100 + n)
+    LU, ipiv, info = oracle.getrf(_np(A))
+    assert info == 0
+    L, U = oracle.unpack_lu(LU)
+    assert np.array_equal(L, L0.numpy())
+    assert np.array_equal(U, U0.numpy())
+    assert np.array_equal(oracle.perm_from_ipiv(ipiv, n), perm.numpy())
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 31, 64, 100])
+def test_dyadic_chol_exact(n):
+    A, L0 = inputs.dyadic_chol(n, seed=200 + n)
+    An = _np(A)
+    L, info = oracle.potrf(An)
+    assert info == 0
+    assert np.array_equal(np.tril(L), L0.numpy())
+    assert np.array_equal(np.triu(L, 1), np.triu(An, 1))
+
+
+@pytest.mark.parametrize("n", [1, 5, 40, 120])
+def test_dyadic_substitution_exact(n):
+    A, L0, U0, perm = inputs.dyadic_lu(n, seed=300 + n)
+    g = torch.Generator().manual_seed(n)
+    X = torch.randint(-4, 5, (n, 3), generator=g).to(torch.float64)
+    B = A @ X
+    LU, ipiv, info = oracle.getrf(_np(A))
+    Xs = oracle.getrs(LU, ipiv, B.numpy())
+    assert np.array_equal(Xs, X.numpy())
+    Ac, Lc = inputs.dyadic_chol(n, seed=400 + n)
+    Bc = Ac @ X
+    Lf, info = oracle.potrf(_np(Ac))
+    assert np.array_equal(oracle.potrs(Lf, Bc.numpy()), X.numpy())
+
+
+# ------------------------------------------------------------------- Cramer
+def _det(M):
+    n = len(M)
+    total = Fraction(0)
+    for p in itertools.permutations(range(n)):
+        inv = sum(1 for a in range(n) for b in range(a + 1, n) if p[a] > p[b])
+        term = Fraction(1)
+        for i in range(n):
+            term *= M[i][p[i]]
+        total += -term if inv % 2 else term
+    return total
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4])
+@pytest.mark.parametrize("seed", range(6))
+def test_cramer(n, seed):
+    g = torch.Generator().manual_seed(1000 * n + seed)
+    while True:
+        Ai = torch.randint(-9, 10, (n, n), generator=g)
+        M = [[Fraction(int(v)) for v in row] for row in Ai.tolist()]
+        D = _det(M)
+        if D != 0:
+            break
+    b = [Fraction(int(v)) for v in torch.randint(-9, 10, (n,), generator=g).tolist()]
+    x_exact = []
+    for k in range(n):
+        Mk = [row[:] for row in M]
+        for i in range(n):
+            Mk[i][k] = b[i]
+        x_exact.append(_det(Mk) / D)
+    # exact inverse for the condition number
+    inv = [[None] * n for _ in range(n)]
+    for j in range(n):
+        e = [Fraction(int(i == j)) for i in range(n)]
+        for k in range(n):
+            Mk = [row[:] for row in M]
+            for i in range(n):
+                Mk[i][k] = e[i]
+            inv[k][j] = _det(Mk) / D
+    anorm = max(sum(abs(v) for v in row) for row in M)
+    ainv = max(sum(abs(v) for v in row) for row in inv)
+    kappa = float(anorm * ainv)
+    A = np.array([[float(v) for v in row] for row in M])
+    LU, ipiv, info = oracle.getrf(A)
+    assert info == 0
+    x = oracle.getrs(LU, ipiv, np.array([float(v) for v in b]))[:, 0]
+    xe = np.array([float(v) for v in x_exact])
+    err = np.abs(x - xe).max() / max(np.abs(xe).max(), 1e-300)
+    assert err <= 4 * n * U64 * kappa + 4 * U64
+
+
+# ----------------------------------------------------------------- invariants
+@pytest.mark.parametrize("n", [50, 200])
+def test_gepp_invariants(n):
+    A = _np(inputs.uniform(n, seed=n))
+    LU, ipiv, info = oracle.getrf(A)
+    assert info == 0
+    L, U = oracle.unpack_lu(LU)
+    p = oracle.perm_from_ipiv(ipiv, n)
+    R = A[p] - L @ U
+    gamma = 3 * n * U64 / (1 - 3 * n * U64)
+    bound = gamma * np.abs(np.abs(L) @ np.abs(U)).sum(axis=1).max()
+    assert np.abs(R).sum(axis=1).max() <= bound
+    assert np.abs(np.tril(LU, -1)).max() <= 1.0
+
+
+@pytest.mark.parametrize("n", [50, 200])
+def test_chol_invariants(n):
+    A = _np(inputs.spd(n, seed=n))
+    L, info = oracle.potrf(A)
+    assert info == 0
+    Lt = np.tril(L)
+    assert (np.diag(Lt) > 0).all()
+    R = A - Lt @ Lt.T
+    assert np.abs(R).max() <= 4 * (n + 1) * U64 * np.abs(Lt @ Lt.T).max() * 4
+
+
+# -------------------------------------------------------------- special cases
+def test_identity_and_diagonal():
+    n = 9
+    LU, ipiv, info = oracle.getrf(np.eye(n))
+    assert info == 0 and list(ipiv) == list(range(1, n + 1))
+    assert np.array_equal(LU, np.eye(n))
+    d = np.diag(np.arange(1.0, n + 1))
+    LU, ipiv, info = oracle.getrf(d)
+    assert list(ipiv) == list(range(1, n + 1)) and np.array_equal(LU, d)
+
+
+def test_permutation_matrix():
+    n = 8
+    perm = np.array([3, 0, 7, 5, 1, 2, 6, 4])
+    P = np.eye(n)[perm]
+    LU, ipiv, info = oracle.getrf(P)
+    assert info == 0
+    assert np.array_equal(LU, np.eye(n))
+    p = oracle.perm_from_ipiv(ipiv, n)
+    assert np.array_equal(P[p], np.eye(n))
+
+
+def test_upper_dominant_no_pivoting():
+    n = 12
+    A = np.triu(np.ones((n, n))) + np.diag(np.full(n, 10.0))
+    LU, ipiv, info = oracle.getrf(A)
+    assert list(ipiv) == list(range(1, n + 1))
+    assert np.array_equal(LU, A)
+
+
+def test_singular_zero_column():
+    n, k = 10, 4
+    A = _np(inputs.uniform(n, seed=7))
+    A[:, k] = 0.0
+    LU, ipiv, info = oracle.getrf(A)
+    assert info == k + 1
+    assert ipiv[k] == k + 1          # idamax of an all-zero column picks the first row
+
+
+def test_not_spd():
+    n, k = 6, 3
+    A = np.eye(n) * 2.0
+    A[k, k] = -1.0
+    L, info = oracle.potrf(A)
+    assert info == k + 1
+
+
+def test_n_one_and_empty():
+    LU, ipiv, info = oracle.getrf(np.array([[-3.0]]))
+    assert info == 0 and list(ipiv) == [1] and LU[0, 0] == -3.0
+    LU, ipiv, info = oracle.getrf(np.zeros((0, 0)))
+    assert info == 0 and len(ipiv) == 0
+
+
+# ------------------------------------------------------------ LAPACK crosscheck
+@pytest.mark.parametrize("n", [10, 100, 512])
+def test_lapack_crosscheck(n):
+    A = inputs.uniform(n, seed=0 if n == 512 else n)
+    LUl, pivl = torch.linalg.lu_factor(A)
+    LU, ipiv, info = oracle.getrf(_np(A))
+    assert oracle.min_pivot_gap(_np(A)) > 1e-10
+    assert np.array_equal(ipiv, pivl.numpy().astype(np.int32))
+    assert np.abs(LU - LUl.numpy()).max() <= 1e-11 * max(1.0, np.abs(LU).max())
+    S = inputs.spd(n, seed=n)
+    L, info = oracle.potrf(_np(S))
+    Ll = torch.linalg.cholesky(S).numpy()
+    assert np.abs(np.tril(L) - Ll).max() <= 1e-12 * np.abs(Ll).max()
+
+
+# ------------------------------------------------------------ backward error
+def test_backward_error_closed_form():
+    A = np.array([[2.0, 0.0], [0.0, 1.0]])
+    x = np.array([1.0, 1.0])
+    b = np.array([2.0, 1.5])
+    # r = (0, 0.5); ||A||_inf = 2; ||x||_inf = 1
+    assert oracle.backward_error(A, x, b)[0] == 0.25
+
+
+def test_backward_error_gepp_small():
+    n = 512
+    A = _np(inputs.uniform(n, seed=0))
+    x_true = np.ones((n, 1))
+    b = A @ x_true
+    LU, ipiv, info = oracle.getrf(A)
+    x = oracle.getrs(LU, ipiv, b)
+    assert oracle.backward_error(A, x, b)[0] <= 1e-14
+
+
+# ----------------------------------------------------------------- gradient
+def test_grad_identity_closed_form():
+    n, k = 5, 2
+    g = np.arange(1.0, n * k + 1).reshape(n, k)
+    b = np.linspace(-1, 1, n * k).reshape(n, k)
+    gA, gB = oracle.solve_grad(np.eye(n), b, g)
+    assert np.array_equal(gB, g)
+    assert np.allclose(gA, -g @ b.T, rtol=4e-16, atol=1e-15)
+
+
+def test_grad_2x2_closed_form():
+    A = np.array([[3.0, 1.0], [2.0, 4.0]])
+    det = 10.0
+    Ainv = np.array([[4.0, -1.0], [-2.0, 3.0]]) / det
+    b = np.array([[1.0], [-2.0]])
+    x = Ainv @ b
+    g = np.array([[0.5], [1.5]])
+    gA, gB = oracle.solve_grad(A, x, g)
+    assert np.allclose(gB, Ainv.T @ g, rtol=4e-16, atol=1e-15)
+    assert np.allclose(gA, -(Ainv.T @ g) @ x.T, rtol=4e-16, atol=1e-15)
+
+
+def test_grad_central_differences():
+    n, k = 6, 2
+    A = _np(inputs.uniform(n, seed=3)) + 3 * np.eye(n)
+    b = np.asfortranarray(np.arange(n * k, dtype=np.float64).reshape(n, k) / 7.0)
+    g = np.asfortranarray(np.cos(np.arange(n * k, dtype=np.float64)).reshape(n, k))
+
+    def f(Am):
+        LU, ipiv, _ = oracle.getrf(Am)
+        return float((oracle.getrs(LU, ipiv, b) * g).sum())
+
+    LU, ipiv, _ = oracle.getrf(A)
+    x = oracle.getrs(LU, ipiv, b)
+    gA, _ = oracle.solve_grad(A, x, g)
+    h = 1e-6
+    for (i, j) in [(0, 0), (2, 5), (5, 1), (3, 3)]:
+        Ap = A.copy(order="F"); Ap[i, j] += h
+        Am = A.copy(order="F"); Am[i, j] -= h
+        fd = (f(Ap) - f(Am)) / (2 * h)
+        assert abs(fd - gA[i, j]) <= 1e-6 * max(1.0, abs(gA[i, j]))

@@ -1,0 +1,130 @@
+"""Pins for the GMRES / GMRES-IR oracle and for the low-precision LU oracle.
+
+* Krylov theory: with k distinct eigenvalues GMRES terminates in k steps and
+  not earlier; the Arnoldi relation A V_k = V_{k+1} H_k holds with V
+  orthonormal; residual norms never increase; full GMRES equals a direct solve.
+* An exact preconditioner makes GMRES converge in one step.
+* Rounding helpers agree with library conversions (numpy float16, torch
+  bfloat16) and with hand-computed TF32 roundings.
+* The low-precision LU recovers exactly representable factors bit for bit in
+  every update precision, and classical theory bounds GMRES-IR's outer steps.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import gmres as G
+from oracle import mixed as M
+from paper_1511_07174_gb300 import inputs
+
+
+def test_gmres_distinct_eigenvalues():
+    n, k = 60, 5
+    rng = np.random.default_rng(0)
+    eig = np.repeat(np.array([1.0, 2.0, 3.5, -1.5, 7.0]), n // k)
+    Q = np.linalg.qr(rng.standard_normal((n, n)))[0]
+    A = Q @ np.diag(eig) @ Q.T
+    b = rng.standard_normal(n)
+    d, steps, hist = G.gmres(lambda v: A @ v, b, m=n, tol=1e-12)
+    assert steps == k
+    assert hist[k - 1] > 1e-6 * np.linalg.norm(b)
+    assert np.linalg.norm(A @ d - b) <= 1e-10 * np.linalg.norm(b)
+
+
+def test_arnoldi_relation():
+    n, k = 40, 12
+    A = inputs.uniform(n, seed=11).numpy()
+    v0 = np.ones(n)
+    V, H = G.arnoldi(lambda v: A @ v, v0, k)
+    assert np.abs(V.T @ V - np.eye(k + 1)).max() <= 1e-13
+    assert np.abs(A @ V[:, :k] - V @ H).max() <= 1e-13
+    assert np.abs(np.tril(H, -2)).max() == 0.0
+
+
+def test_gmres_monotone_and_full():
+    n = 30
+    A = inputs.uniform(n, seed=12).numpy() + 2 * np.eye(n)
+    b = np.sin(np.arange(n, dtype=np.float64))
+    d, steps, hist = G.gmres(lambda v: A @ v, b, m=n, tol=1e-14)
+    assert all(hist[i + 1] <= hist[i] * (1 + 1e-12) for i in range(len(hist) - 1))
+    assert np.abs(d - np.linalg.solve(A, b)).max() <= 1e-10
+
+
+def test_gmres_restart_converges():
+    n = 50
+    A = inputs.uniform(n, seed=13).numpy() + 8 * np.eye(n)
+    b = np.ones(n)
+    d, steps, hist = G.gmres(lambda v: A @ v, b, m=5, tol=1e-12, restarts=40)
+    assert np.linalg.norm(A @ d - b) <= 1e-11 * np.linalg.norm(b)
+
+
+def test_gmres_exact_preconditioner_one_step():
+    n = 64
+    A = inputs.uniform(n, seed=14).numpy()
+    LU, ipiv, _ = oracle.getrf(np.asfortranarray(A))
+    minv = lambda v: oracle.getrs(LU, ipiv, v)[:, 0]
+    r = np.cos(np.arange(n, dtype=np.float64))
+    d, steps, hist = G.gmres(lambda v: minv(A @ v), minv(r), m=20, tol=1e-10)
+    assert steps == 1
+
+
+def test_round_helpers_against_libraries():
+    rng = np.random.default_rng(1)
+    x = (rng.standard_normal(10000) * 10.0 ** rng.integers(-6, 4, 10000)).astype(np.float32)
+    bt = torch.from_numpy(x).to(torch.bfloat16).to(torch.float32).numpy().astype(np.float64)
+    assert np.array_equal(M.round_bf16(x), bt)
+    assert np.array_equal(M.round_fp16(x), x.astype(np.float16).astype(np.float64))
+    # TF32 keeps 10 explicit mantissa bits; halfway cases round away from zero
+    one = np.float32(1.0)
+    tests = {1.0 + 2.0 ** -11: 1.0 + 2.0 ** -10,          # tie -> away
+             1.0 + 2.0 ** -12: 1.0,                       # below half -> down
+             -(1.0 + 3 * 2.0 ** -11): -(1.0 + 2 * 2.0 ** -10),
+             1.0 + 2.0 ** -10: 1.0 + 2.0 ** -10}
+    for v, want in tests.items():
+        assert M.round_tf32(np.array([v], dtype=np.float32))[0] == want
+    assert one == 1.0
+
+
+def test_sliver_exponent_range():
+    vals = np.array([1e-20, 3e-5, 0.7, 1.0, 1234.5, 6e4, 2.0 ** 14, 2.0 ** 15 - 1])
+    e = M.sliver_exponent(vals)
+    s = np.ldexp(vals, e)
+    assert ((s >= 2.0 ** 14) & (s < 2.0 ** 15)).all()
+    assert M.sliver_exponent(np.array([0.0]))[0] == 0
+    assert M.sliver_exponent(np.array([1e-35]))[0] == M.SCALE_CLAMP     # clamped
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16", "fp16"])
+@pytest.mark.parametrize("n,nb", [(1, 4), (37, 8), (96, 32)])
+def test_lowprec_lu_dyadic_exact(prec, n, nb):
+    A, L0, U0, perm = inputs.dyadic_lu(n, seed=500 + n)
+    W, ipiv, info = M.lu_lowprec(A.numpy(), nb, prec)
+    L, U = oracle.unpack_lu(W)
+    assert info == 0
+    assert np.array_equal(L, L0.numpy()) and np.array_equal(U, U0.numpy())
+    assert np.array_equal(oracle.perm_from_ipiv(ipiv, n), perm.numpy())
+
+
+def test_lowprec_lu_fp32_close_to_fp64():
+    n = 128
+    A = inputs.uniform(n, seed=0).numpy()
+    W, ipiv, info = M.lu_lowprec(A, 32, "fp32")
+    LU, ipiv64, _ = oracle.getrf(np.asfortranarray(A))
+    assert np.array_equal(ipiv, ipiv64)
+    assert np.abs(W - LU).max() <= 1e-4 * np.abs(LU).max()
+
+
+@pytest.mark.parametrize("prec,kappa,max_outer", [("fp32", 1e2, 3), ("bf16", 1e4, 10),
+                                                   ("fp16", 1e4, 10)])
+def test_gmres_ir_oracle_converges(prec, kappa, max_outer):
+    n = 160
+    A = inputs.haar_kappa(n, kappa, seed_u=4, seed_v=5).numpy()
+    x_true = inputs.normal((n,), 6).numpy()
+    b = A @ x_true
+    W, ipiv, info = M.lu_lowprec(A, 32, prec)
+    x, st = G.gmres_ir(A, b, M.apply_minv_factory(W, ipiv), tol=1e-14, m=50, tau=1e-8,
+                       max_outer=max_outer)
+    assert st["converged"], st
+    assert oracle.backward_error(A, x, b)[0] <= 1e-14
+    assert np.abs(x - x_true).max() <= 1e-14 * kappa * 100 * np.abs(x_true).max()
