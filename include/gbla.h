@@ -1,0 +1,164 @@
+/*
+ * gbla -- dense LU / Cholesky solvers for one GB300 GPU (sm_103a), C ABI.
+ *
+ * The operations are those of the paper's direct method (Oancea & Andrei,
+ * "Developing a High Performance Software Library with MPI and CUDA for Matrix
+ * Computations", section 2): factor A = LU with partial pivoting (or A = L L^t
+ * for SPD A), then solve L y = b and U x = y by forward and back substitution;
+ * the factorisation is blocked by delayed updating (k rank-1 updates replaced
+ * by one rank-k update). The mixed-precision variant factors in low precision
+ * and recovers FP64 accuracy by GMRES (section 2: Gram-Schmidt, restarted)
+ * used as the inner solver of iterative refinement.
+ *
+ * Conventions for every entry point
+ *   - Matrices are column-major: element (i, j) of A is A[i + j*lda], 0-based,
+ *     lda >= max(1, n). Pivots are LAPACK getrf style: 1-based, row j was
+ *     interchanged with row ipiv[j] at step j, applied in order j = 0..n-1.
+ *   - Every pointer is a DEVICE pointer owned by the caller unless stated
+ *     otherwise. The library allocates no device memory: calls that need
+ *     scratch take a caller-provided device workspace of at least the size
+ *     the matching *_workspace function returns (256-byte aligned).
+ *   - Every call is enqueued on `stream` (a cudaStream_t; NULL = the legacy
+ *     default stream) and returns without waiting, except where stated.
+ *   - Return value: 0 on success; -i when argument i (1-based) is invalid,
+ *     nothing enqueued; a positive GBLA_ERR_* code otherwise.
+ *   - Numerical outcome is written to a device int `d_info` (0 = success;
+ *     k > 0 = the first exact zero pivot / non-positive leading minor at
+ *     1-based k; GBLA_INFO_TIMEOUT when an inter-CTA wait gave up). The
+ *     timeout code replaces only a zero.
+ */
+#ifndef GBLA_H
+#define GBLA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *gbla_stream_t; /* same type as cudaStream_t */
+
+#define GBLA_OK 0
+#define GBLA_ERR_WORKSPACE 1001     /* workspace NULL, misaligned or too small */
+#define GBLA_ERR_CUDA 1002          /* a CUDA runtime call (launch, copy, query) failed */
+#define GBLA_ERR_DEVICE 1003        /* device lacks a needed capability (cooperative launch) */
+#define GBLA_ERR_NOT_CONVERGED 1004 /* refinement stopped before reaching the tolerance */
+#define GBLA_ERR_TIMEOUT 1005       /* host-visible: a device wait gave up (see d_info) */
+#define GBLA_ERR_INTERNAL 1006
+
+#define GBLA_INFO_TIMEOUT (-1000)
+
+/* Precision of the trailing-matrix update of the mixed factorisation. */
+#define GBLA_PREC_FP32 1 /* FP32 operands, FP32 FMA (SIMT) */
+#define GBLA_PREC_TF32 2 /* TF32 operands (nearest, ties away), FP32 accumulate, tensor cores */
+#define GBLA_PREC_BF16 3 /* BF16 operands with power-of-two row/column scaling, FP32 accumulate */
+#define GBLA_PREC_FP16 4 /* FP16 operands with power-of-two row/column scaling, FP32 accumulate */
+
+/* Library version string (static storage). */
+const char *gbla_version(void);
+
+/* Human-readable text for a return code (static storage). */
+const char *gbla_status_string(int status);
+
+/*
+ * Limit, in nanoseconds, for every inter-CTA wait of later calls (panel
+ * barrier, substitution chain). A wait that runs out writes GBLA_INFO_TIMEOUT
+ * to d_info and the kernel returns. Default 2e9 (2 s). Process-wide; not
+ * thread-safe against concurrent calls.
+ */
+void gbla_set_wait_timeout_ns(uint64_t ns);
+uint64_t gbla_get_wait_timeout_ns(void);
+
+/* ------------------------------------------------------------------------
+ * FP64 LU with partial pivoting (paper section 2; steps a1-a4).
+ * Blocked right-looking: for each block column of width nb the panel is
+ * factored by a cooperative kernel (warp-shuffle argmax pivot search, row
+ * swaps and scaling on a shared-memory-resident slab, one grid barrier per
+ * column), the interchanges are applied to the other columns, the U row
+ * block is solved against the unit lower diagonal block, and the trailing
+ * matrix receives one rank-nb update.
+ *   n      order of A (n >= 0)
+ *   A      n x n, overwritten by L (strict lower, unit diagonal implied) and U
+ *   lda    leading dimension (>= max(1, n))
+ *   ipiv   n ints, output pivots (1-based)
+ *   d_info one int, output (see conventions); set to 0 by the call
+ *   nb     block size in [32, 512], multiple of 32; 0 = default (256)
+ * ------------------------------------------------------------------------ */
+size_t gbla_lu_factor_workspace(int n, int nb);
+int gbla_lu_factor(int n, double *A, int lda, int *ipiv, int *d_info, int nb,
+                   void *d_work, size_t work_bytes, gbla_stream_t stream);
+
+/*
+ * Solve op(A) X = B from the gbla_lu_factor output (paper section 2, steps
+ * a5-a6): trans = 0: apply P, L y = Pb (unit, forward), U x = y (back);
+ * trans = 1: A^t x = b via U^t z = b, L^t w = z, x = P^t w.
+ * B (n x nrhs, ldb) is overwritten by X. Needs d_info (one int, set to 0;
+ * receives GBLA_INFO_TIMEOUT if a chain wait gave up).
+ */
+size_t gbla_lu_solve_workspace(int n, int nrhs);
+int gbla_lu_solve(int trans, int n, int nrhs, const double *LU, int lda, const int *ipiv,
+                  double *B, int ldb, int *d_info, void *d_work, size_t work_bytes,
+                  gbla_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Mixed-precision LU (steps a1-a4 in low precision). F (n x n FP32, ldf) is
+ * set to fp32(A) and factored in place: panels in FP64 arithmetic rounded to
+ * FP32, the U row block by FP32 substitution, the trailing update in the
+ * precision `prec` (GBLA_PREC_*): tensor-core (tcgen05, TMEM accumulator,
+ * TMA-fed) for TF32 / BF16 / FP16, FP32 SIMT for FP32. BF16 / FP16 operands
+ * carry one power-of-two scale per row of L21 and per column of U12, undone
+ * exactly in the epilogue. A (FP64) is only read.
+ * ------------------------------------------------------------------------ */
+size_t gbla_lu_factor_mixed_workspace(int n, int nb, int prec);
+int gbla_lu_factor_mixed(int n, const double *A, int lda, float *F, int ldf, int *ipiv,
+                         int *d_info, int prec, int nb, void *d_work, size_t work_bytes,
+                         gbla_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * GMRES-based iterative refinement (step a7-a8) for one right-hand side:
+ * x0 = M^{-1} b with M = P^t L U from gbla_lu_factor_mixed (FP32 factors,
+ * FP64 arithmetic); then repeat r = b - A x (FP64), stop when
+ * ||r||_inf / (||A||_inf ||x||_inf) <= tol; otherwise run GMRES(m) (modified
+ * Gram-Schmidt, Givens rotations) on M^{-1} A d = M^{-1} r from d = 0 until
+ * the least-squares residual falls below inner_tol * ||M^{-1} r||_2, and set
+ * x <- x + d (FP64).
+ * SYNCHRONOUS: reads one scalar back per inner step and per outer step
+ * (it synchronises `stream`). Host pointers: opts, stats.
+ * Returns 0 when converged, GBLA_ERR_NOT_CONVERGED otherwise (x holds the
+ * last iterate), GBLA_ERR_TIMEOUT when a kernel wait gave up.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  double tol;       /* normwise backward-error target, e.g. 1e-14 */
+  double inner_tol; /* GMRES relative tolerance, e.g. 1e-8 */
+  int max_outer;    /* refinement steps, e.g. 10 */
+  int restart_m;    /* GMRES Krylov dimension per call, 1..128, e.g. 50 */
+} gbla_gmresir_opts;
+
+typedef struct {
+  int outer;      /* refinement steps taken */
+  int inner;      /* GMRES steps in total */
+  int converged;  /* 1 when beta <= tol */
+  double beta;    /* final normwise backward error */
+  double beta0;   /* backward error of x0 */
+} gbla_gmresir_stats;
+
+size_t gbla_gmresir_workspace(int n, int restart_m);
+int gbla_gmresir_solve(int n, const double *A, int lda, const float *F, int ldf,
+                       const int *ipiv, const double *b, double *x,
+                       const gbla_gmresir_opts *opts, gbla_gmresir_stats *stats,
+                       void *d_work, size_t work_bytes, gbla_stream_t stream);
+
+/*
+ * Normwise backward error per column (step a7): d_beta[c] =
+ * ||B(:,c) - A X(:,c)||_inf / (||A||_inf ||X(:,c)||_inf), FP64, on the device.
+ */
+size_t gbla_backward_error_workspace(int n, int nrhs);
+int gbla_backward_error(int n, int nrhs, const double *A, int lda, const double *X, int ldx,
+                        const double *B, int ldb, double *d_beta, void *d_work,
+                        size_t work_bytes, gbla_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBLA_H */

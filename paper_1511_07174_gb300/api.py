@@ -1,0 +1,169 @@
+"""Python entry points over the C ABI (include/gbla.h).
+
+Each function takes CUDA tensors, passes their device pointers, sizes and the
+current torch stream to the matching gbla_* call, and returns tensors. Matrices
+use the usual A[i, j] indexing; storage handed to the library is column-major
+(stride (1, n)). Workspaces are torch allocations on the same stream.
+"""
+import ctypes
+
+import torch
+
+from . import _lib
+
+PREC = _lib.GBLA_PREC
+
+
+class GblaError(RuntimeError):
+    def __init__(self, name, rc):
+        self.rc = rc
+        super().__init__("%s failed: %d (%s)" % (name, rc, _lib.status_string(rc)))
+
+
+def _check(name, rc):
+    if rc != 0:
+        raise GblaError(name, rc)
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _p(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else ctypes.c_void_p(0)
+
+
+def _is_colmajor(A):
+    n, m = A.shape
+    return A.stride(0) == 1 and (A.stride(1) >= max(1, n) or m <= 1)
+
+
+def colmajor(A, dtype=None, copy=False):
+    """Column-major version of a 2-D tensor (a copy when copy=True or when needed)."""
+    dtype = dtype or A.dtype
+    if A.dim() == 1:
+        A = A.unsqueeze(1)
+    if not copy and A.dtype == dtype and _is_colmajor(A):
+        return A
+    out = torch.empty_strided(A.shape, (1, max(1, A.shape[0])), dtype=dtype, device=A.device)
+    out.copy_(A)
+    return out
+
+
+def _ld(A):
+    return max(1, A.stride(1)) if A.shape[1] > 1 else max(1, A.shape[0])
+
+
+def _ws(nbytes, device):
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def _require_cuda(*ts):
+    for t in ts:
+        if t is not None and not t.is_cuda:
+            raise ValueError("gbla works on CUDA tensors only (no CPU path)")
+
+
+def set_wait_timeout_ns(ns):
+    _lib.load().gbla_set_wait_timeout_ns(int(ns))
+
+
+def get_wait_timeout_ns():
+    return int(_lib.load().gbla_get_wait_timeout_ns())
+
+
+# ---------------------------------------------------------------------- LU FP64
+def lu_factor(A, nb=0):
+    """P A = L U (FP64, partial pivoting). Returns (LU, ipiv int32 1-based, info device int32[1])."""
+    _require_cuda(A)
+    L = _lib.load()
+    n = A.shape[0]
+    LU = colmajor(A, torch.float64, copy=True)
+    ipiv = torch.empty(max(n, 1), dtype=torch.int32, device=A.device)
+    info = torch.zeros(1, dtype=torch.int32, device=A.device)
+    ws = _ws(L.gbla_lu_factor_workspace(n, nb), A.device)
+    _check("gbla_lu_factor", L.gbla_lu_factor(n, _p(LU), _ld(LU), _p(ipiv), _p(info), nb, _p(ws),
+                                              ws.numel(), _stream()))
+    return LU, ipiv[:n], info
+
+
+def lu_solve(LU, ipiv, B, trans=False, info=None):
+    """Solve A X = B (or A^t X = B) from lu_factor's output. Returns X (column-major)."""
+    _require_cuda(LU, ipiv, B)
+    L = _lib.load()
+    n = LU.shape[0]
+    vec = B.dim() == 1
+    X = colmajor(B, torch.float64, copy=True)
+    nrhs = X.shape[1]
+    info = torch.zeros(1, dtype=torch.int32, device=B.device) if info is None else info
+    LUc = colmajor(LU, torch.float64)
+    ws = _ws(L.gbla_lu_solve_workspace(n, nrhs), B.device)
+    _check("gbla_lu_solve", L.gbla_lu_solve(1 if trans else 0, n, nrhs, _p(LUc), _ld(LUc), _p(ipiv),
+                                            _p(X), _ld(X), _p(info), _p(ws), ws.numel(), _stream()))
+    return X[:, 0] if vec else X
+
+
+# ------------------------------------------------------------------ mixed path
+def lu_factor_mixed(A, prec="bf16", nb=256, F=None):
+    """Low-precision LU of fp32(A): returns (F FP32 factors, ipiv, info)."""
+    _require_cuda(A)
+    L = _lib.load()
+    n = A.shape[0]
+    Ac = colmajor(A, torch.float64)
+    if F is None:
+        F = torch.empty_strided((n, n), (1, max(1, n)), dtype=torch.float32, device=A.device)
+    ipiv = torch.empty(max(n, 1), dtype=torch.int32, device=A.device)
+    info = torch.zeros(1, dtype=torch.int32, device=A.device)
+    p = PREC[prec] if isinstance(prec, str) else int(prec)
+    ws = _ws(L.gbla_lu_factor_mixed_workspace(n, nb, p), A.device)
+    _check("gbla_lu_factor_mixed",
+           L.gbla_lu_factor_mixed(n, _p(Ac), _ld(Ac), _p(F), _ld(F), _p(ipiv), _p(info), p, nb,
+                                  _p(ws), ws.numel(), _stream()))
+    return F, ipiv[:n], info
+
+
+def gmresir(A, F, ipiv, b, tol=1e-14, inner_tol=1e-8, max_outer=10, restart_m=50, x=None):
+    """GMRES-based refinement of A x = b with the mixed factors. Synchronous.
+    Returns (x, stats dict); raises GblaError on a hard failure, not on non-convergence."""
+    _require_cuda(A, F, ipiv, b)
+    L = _lib.load()
+    n = A.shape[0]
+    Ac = colmajor(A, torch.float64)
+    Fc = colmajor(F, torch.float32)
+    bc = b.reshape(-1).to(torch.float64).contiguous()
+    x = torch.empty(max(n, 1), dtype=torch.float64, device=A.device) if x is None else x
+    opts = _lib.GmresirOpts(tol, inner_tol, max_outer, restart_m)
+    st = _lib.GmresirStats()
+    ws = _ws(L.gbla_gmresir_workspace(n, restart_m), A.device)
+    rc = L.gbla_gmresir_solve(n, _p(Ac), _ld(Ac), _p(Fc), _ld(Fc), _p(ipiv), _p(bc), _p(x),
+                              ctypes.byref(opts), ctypes.byref(st), _p(ws), ws.numel(), _stream())
+    if rc not in (0, _lib.GBLA_ERR_NOT_CONVERGED):
+        raise GblaError("gbla_gmresir_solve", rc)
+    stats = {"outer": st.outer, "inner": st.inner, "converged": bool(st.converged),
+             "beta": st.beta, "beta0": st.beta0}
+    return x[:n], stats
+
+
+def solve_mixed(A, b, prec="bf16", nb=256, **kw):
+    """Mixed-precision LU + GMRES-IR. Returns (x, stats)."""
+    F, ipiv, info = lu_factor_mixed(A, prec, nb)
+    x, st = gmresir(A, F, ipiv, b, **kw)
+    st["info"] = int(info.item())
+    return x, st
+
+
+def backward_error(A, X, B):
+    """Per-column ||B - A X||_inf / (||A||_inf ||X||_inf) on the device (FP64)."""
+    _require_cuda(A, X, B)
+    L = _lib.load()
+    n = A.shape[0]
+    Ac = colmajor(A, torch.float64)
+    Xc = colmajor(X, torch.float64)
+    Bc = colmajor(B, torch.float64)
+    nrhs = Xc.shape[1]
+    beta = torch.empty(max(nrhs, 1), dtype=torch.float64, device=A.device)
+    ws = _ws(L.gbla_backward_error_workspace(n, nrhs), A.device)
+    _check("gbla_backward_error",
+           L.gbla_backward_error(n, nrhs, _p(Ac), _ld(Ac), _p(Xc), _ld(Xc), _p(Bc), _ld(Bc), _p(beta),
+                                 _p(ws), ws.numel(), _stream()))
+    return beta[:nrhs]

@@ -1,0 +1,481 @@
+// C ABI of libgbla: argument checks, workspace carving and the host-side
+// schedule of the blocked factorisations (paper section 2: factor, then the two
+// triangular solves; blocked by delayed updating) and of the GMRES-based
+// refinement. Every numerical step runs in the kernels of this library.
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "internal.h"
+
+namespace gbla {
+
+static uint64_t g_wait_ns = 2000000000ull;
+uint64_t wait_timeout_ns() { return g_wait_ns; }
+
+const DeviceProps& device_props() {
+  static DeviceProps props[64];
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    static DeviceProps none;
+    return none;
+  }
+  DeviceProps& p = props[dev];
+  if (p.device < 0) {
+    int sms = 0, coop = 0, optin = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    p.num_sms = sms;
+    p.coop = coop;
+    p.smem_optin = (size_t)optin;
+    p.device = dev;
+  }
+  return p;
+}
+
+static int cuda_status(cudaError_t e) { return e == cudaSuccess ? GBLA_OK : GBLA_ERR_CUDA; }
+
+#define GBLA_TRY(expr)                       \
+  do {                                       \
+    cudaError_t _e = (expr);                 \
+    if (_e != cudaSuccess) return GBLA_ERR_CUDA; \
+  } while (0)
+
+static bool aligned256(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 255) == 0; }
+
+static int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+// ----------------------------------------------------------------------------
+// Blocked right-looking LU over a generic storage type. Outer blocks of width
+// nb; inside each, inner panels of width kPanelWidth factored by the
+// cooperative kernel, followed by the inner interchanges, substitution and
+// update restricted to the outer block. After the outer block: interchanges
+// on the rest of the matrix, the U row block, and the trailing update.
+struct LuWork {
+  double* slots;
+  unsigned* counters;
+  // mixed path only
+  void* Ak;
+  void* Bk;
+  int* eA;
+  int* eB;
+  int ldk;
+};
+
+static size_t lu_work_layout(Carver& c, int n, int nb, int prec, LuWork* w) {
+  const int npanels = ceil_div(std::max(n, 1), kPanelWidth);
+  double* slots = c.take<double>(panel_slots_doubles());
+  unsigned* counters = c.take<unsigned>((size_t)npanels + 1);
+  if (w) {
+    w->slots = slots;
+    w->counters = counters;
+    w->Ak = w->Bk = nullptr;
+    w->eA = w->eB = nullptr;
+    w->ldk = 0;
+  }
+  if (prec == GBLA_PREC_BF16 || prec == GBLA_PREC_FP16 || prec == GBLA_PREC_TF32) {
+    const int elem = prec == GBLA_PREC_TF32 ? 4 : 2;
+    const int ldk = ((nb + 63) / 64) * 64;
+    void* Ak = c.take<char>((size_t)std::max(n, 1) * ldk * elem);
+    void* Bk = c.take<char>((size_t)std::max(n, 1) * ldk * elem);
+    int* eA = c.take<int>((size_t)std::max(n, 1));
+    int* eB = c.take<int>((size_t)std::max(n, 1));
+    if (w) {
+      w->Ak = Ak;
+      w->Bk = Bk;
+      w->eA = eA;
+      w->eB = eB;
+      w->ldk = ldk;
+    }
+  }
+  return c.off;
+}
+
+template <typename Ts>
+static cudaError_t blocked_lu(int n, Ts* A, int lda, int* ipiv, int* info, int nb, int prec,
+                              const LuWork& w, cudaStream_t s) {
+  typedef Ts Tc_trsm;  // substitution arithmetic: FP64 for FP64 storage, FP32 for FP32
+  cudaError_t e;
+  for (int k0 = 0; k0 < n; k0 += nb) {
+    const int kb = std::min(nb, n - k0);
+    for (int j0 = k0; j0 < k0 + kb; j0 += kPanelWidth) {
+      const int jb = std::min(kPanelWidth, k0 + kb - j0);
+      e = launch_panel<Ts>(A + j0 + (size_t)j0 * lda, lda, n - j0, jb, j0, ipiv + j0, info,
+                           w.slots, w.counters + j0 / kPanelWidth, s);
+      if (e != cudaSuccess) return e;
+      e = launch_laswp<Ts>(A, lda, n, k0, j0, j0 + jb, k0 + kb, ipiv, j0, j0 + jb, s);
+      if (e != cudaSuccess) return e;
+      const int nrest = k0 + kb - j0 - jb;
+      if (nrest > 0) {
+        e = launch_trsm_lunit<Ts, Tc_trsm>(A + j0 + (size_t)j0 * lda, lda,
+                                           A + j0 + (size_t)(j0 + jb) * lda, lda, jb, nrest, 0,
+                                           nullptr, 0, nullptr, s);
+        if (e != cudaSuccess) return e;
+        e = launch_gemm_simt<Ts>(n - j0 - jb, nrest, jb, (Ts)-1, A + (j0 + jb) + (size_t)j0 * lda,
+                                 lda, A + j0 + (size_t)(j0 + jb) * lda, lda, false, (Ts)1,
+                                 A + (j0 + jb) + (size_t)(j0 + jb) * lda, lda, false, s);
+        if (e != cudaSuccess) return e;
+      }
+    }
+    e = launch_laswp<Ts>(A, lda, n, 0, k0, k0 + kb, n, ipiv, k0, k0 + kb, s);
+    if (e != cudaSuccess) return e;
+    const int nt = n - k0 - kb;
+    if (nt <= 0) continue;
+    const bool tensor = (prec == GBLA_PREC_BF16 || prec == GBLA_PREC_FP16 || prec == GBLA_PREC_TF32);
+    e = launch_trsm_lunit<Ts, Tc_trsm>(A + k0 + (size_t)k0 * lda, lda, A + k0 + (size_t)(k0 + kb) * lda,
+                                       lda, kb, nt, tensor ? prec : 0, w.Bk, w.ldk, w.eB, s);
+    if (e != cudaSuccess) return e;
+    if (tensor) {
+      if constexpr (sizeof(Ts) == 4) {
+        e = launch_convert_rows(reinterpret_cast<const float*>(A + (k0 + kb) + (size_t)k0 * lda), lda,
+                                nt, kb, prec, w.Ak, w.ldk, w.eA, s);
+        if (e != cudaSuccess) return e;
+        e = launch_gemm_tc(prec, nt, nt, kb, w.Ak, w.ldk, w.Bk, w.ldk, w.eA, w.eB,
+                           reinterpret_cast<float*>(A + (k0 + kb) + (size_t)(k0 + kb) * lda), lda,
+                           info, s);
+        if (e != cudaSuccess) return e;
+      } else {
+        return cudaErrorInvalidValue;
+      }
+    } else {
+      e = launch_gemm_simt<Ts>(nt, nt, kb, (Ts)-1, A + (k0 + kb) + (size_t)k0 * lda, lda,
+                               A + k0 + (size_t)(k0 + kb) * lda, lda, false, (Ts)1,
+                               A + (k0 + kb) + (size_t)(k0 + kb) * lda, lda, false, s);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+static int check_nb(int nb) { return nb == 0 ? 256 : ((nb % 32 == 0 && nb >= 32 && nb <= 256) ? nb : -1); }
+
+}  // namespace gbla
+
+using namespace gbla;
+
+extern "C" {
+
+const char* gbla_version(void) { return "gbla 0.1.0 (sm_103a)"; }
+
+const char* gbla_status_string(int status) {
+  switch (status) {
+    case GBLA_OK: return "success";
+    case GBLA_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case GBLA_ERR_CUDA: return "CUDA runtime call failed";
+    case GBLA_ERR_DEVICE: return "device lacks a required capability";
+    case GBLA_ERR_NOT_CONVERGED: return "refinement did not reach the tolerance";
+    case GBLA_ERR_TIMEOUT: return "a device-side wait gave up";
+    case GBLA_ERR_INTERNAL: return "internal error";
+    default: return status < 0 ? "invalid argument" : "unknown status";
+  }
+}
+
+void gbla_set_wait_timeout_ns(uint64_t ns) { g_wait_ns = ns; }
+uint64_t gbla_get_wait_timeout_ns(void) { return g_wait_ns; }
+
+// ---------------------------------------------------------------------------
+size_t gbla_lu_factor_workspace(int n, int nb) {
+  nb = check_nb(nb);
+  if (n < 0 || nb < 0) return 0;
+  Carver c(nullptr, 0);
+  return lu_work_layout(c, n, nb, 0, nullptr);
+}
+
+int gbla_lu_factor(int n, double* A, int lda, int* ipiv, int* d_info, int nb, void* d_work,
+                   size_t work_bytes, gbla_stream_t stream) {
+  if (n < 0) return -1;
+  if (n > 0 && !A) return -2;
+  if (lda < std::max(1, n)) return -3;
+  if (n > 0 && !ipiv) return -4;
+  if (!d_info) return -5;
+  nb = check_nb(nb);
+  if (nb < 0) return -6;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!d_work || !aligned256(d_work)) return GBLA_ERR_WORKSPACE;
+  Carver c(d_work, work_bytes);
+  LuWork w;
+  lu_work_layout(c, n, nb, 0, &w);
+  if (!c.ok) return GBLA_ERR_WORKSPACE;
+  const DeviceProps& dp = device_props();
+  if (dp.device < 0) return GBLA_ERR_CUDA;
+  if (!dp.coop) return GBLA_ERR_DEVICE;
+  GBLA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), s));
+  if (n == 0) return GBLA_OK;
+  GBLA_TRY(cudaMemsetAsync(w.counters, 0, sizeof(unsigned) * (size_t)(ceil_div(n, kPanelWidth) + 1), s));
+  return cuda_status(blocked_lu<double>(n, A, lda, ipiv, d_info, nb, 0, w, s));
+}
+
+// ---------------------------------------------------------------------------
+size_t gbla_lu_factor_mixed_workspace(int n, int nb, int prec) {
+  nb = check_nb(nb);
+  if (n < 0 || nb < 0 || prec < GBLA_PREC_FP32 || prec > GBLA_PREC_FP16) return 0;
+  Carver c(nullptr, 0);
+  return lu_work_layout(c, n, nb, prec, nullptr);
+}
+
+int gbla_lu_factor_mixed(int n, const double* A, int lda, float* F, int ldf, int* ipiv, int* d_info,
+                         int prec, int nb, void* d_work, size_t work_bytes, gbla_stream_t stream) {
+  if (n < 0) return -1;
+  if (n > 0 && !A) return -2;
+  if (lda < std::max(1, n)) return -3;
+  if (n > 0 && !F) return -4;
+  if (ldf < std::max(1, n)) return -5;
+  if (n > 0 && !ipiv) return -6;
+  if (!d_info) return -7;
+  if (prec < GBLA_PREC_FP32 || prec > GBLA_PREC_FP16) return -8;
+  nb = check_nb(nb);
+  if (nb < 0) return -9;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!d_work || !aligned256(d_work)) return GBLA_ERR_WORKSPACE;
+  Carver c(d_work, work_bytes);
+  LuWork w;
+  lu_work_layout(c, n, nb, prec, &w);
+  if (!c.ok) return GBLA_ERR_WORKSPACE;
+  const DeviceProps& dp = device_props();
+  if (dp.device < 0) return GBLA_ERR_CUDA;
+  if (!dp.coop) return GBLA_ERR_DEVICE;
+  GBLA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), s));
+  if (n == 0) return GBLA_OK;
+  GBLA_TRY(cudaMemsetAsync(w.counters, 0, sizeof(unsigned) * (size_t)(ceil_div(n, kPanelWidth) + 1), s));
+  GBLA_TRY(launch_copy_d2f(A, lda, F, ldf, n, n, s));
+  return cuda_status(blocked_lu<float>(n, F, ldf, ipiv, d_info, nb, prec, w, s));
+}
+
+// ---------------------------------------------------------------------------
+size_t gbla_lu_solve_workspace(int n, int nrhs) {
+  if (n < 0 || nrhs < 0) return 0;
+  Carver c(nullptr, 0);
+  c.take<int>((size_t)std::max(n, 1));
+  c.take<double>((size_t)std::max(n, 1) * std::max(nrhs, 1));
+  c.take<unsigned>(trsv_flags_count(std::max(n, 1)));
+  return c.off;
+}
+
+int gbla_lu_solve(int trans, int n, int nrhs, const double* LU, int lda, const int* ipiv, double* B,
+                  int ldb, int* d_info, void* d_work, size_t work_bytes, gbla_stream_t stream) {
+  if (trans != 0 && trans != 1) return -1;
+  if (n < 0) return -2;
+  if (nrhs < 0) return -3;
+  if (n > 0 && !LU) return -4;
+  if (lda < std::max(1, n)) return -5;
+  if (n > 0 && !ipiv) return -6;
+  if (n > 0 && nrhs > 0 && !B) return -7;
+  if (ldb < std::max(1, n)) return -8;
+  if (!d_info) return -9;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!d_work || !aligned256(d_work)) return GBLA_ERR_WORKSPACE;
+  Carver c(d_work, work_bytes);
+  int* perm = c.take<int>((size_t)std::max(n, 1));
+  double* T = c.take<double>((size_t)std::max(n, 1) * std::max(nrhs, 1));
+  unsigned* flags = c.take<unsigned>(trsv_flags_count(std::max(n, 1)));
+  if (!c.ok) return GBLA_ERR_WORKSPACE;
+  GBLA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), s));
+  if (n == 0 || nrhs == 0) return GBLA_OK;
+  GBLA_TRY(launch_ipiv_to_perm(n, ipiv, perm, s));
+  const int ldt = n;
+  if (!trans) {
+    GBLA_TRY(launch_permute_rows(n, nrhs, perm, false, B, ldb, T, ldt, s));
+    GBLA_TRY(launch_trsv<double>(true, false, true, n, nrhs, LU, lda, T, ldt, flags, d_info, s));
+    GBLA_TRY(launch_trsv<double>(false, false, false, n, nrhs, LU, lda, T, ldt, flags, d_info, s));
+    GBLA_TRY(cudaMemcpy2DAsync(B, sizeof(double) * ldb, T, sizeof(double) * ldt, sizeof(double) * n,
+                               nrhs, cudaMemcpyDeviceToDevice, s));
+  } else {
+    GBLA_TRY(cudaMemcpy2DAsync(T, sizeof(double) * ldt, B, sizeof(double) * ldb, sizeof(double) * n,
+                               nrhs, cudaMemcpyDeviceToDevice, s));
+    GBLA_TRY(launch_trsv<double>(false, true, false, n, nrhs, LU, lda, T, ldt, flags, d_info, s));
+    GBLA_TRY(launch_trsv<double>(true, true, true, n, nrhs, LU, lda, T, ldt, flags, d_info, s));
+    GBLA_TRY(launch_permute_rows(n, nrhs, perm, true, T, ldt, B, ldb, s));
+  }
+  return GBLA_OK;
+}
+
+// ---------------------------------------------------------------------------
+size_t gbla_backward_error_workspace(int n, int nrhs) {
+  if (n < 0 || nrhs < 0) return 0;
+  Carver c(nullptr, 0);
+  c.take<double>((size_t)std::max(n, 1) * std::max(nrhs, 1));
+  c.take<double>(residual_work_doubles(std::max(n, 1), std::min(std::max(nrhs, 1), 8)));
+  c.take<double>(1);
+  return c.off;
+}
+
+int gbla_backward_error(int n, int nrhs, const double* A, int lda, const double* X, int ldx,
+                        const double* B, int ldb, double* d_beta, void* d_work, size_t work_bytes,
+                        gbla_stream_t stream) {
+  if (n < 0) return -1;
+  if (nrhs < 0) return -2;
+  if (n > 0 && !A) return -3;
+  if (lda < std::max(1, n)) return -4;
+  if (n > 0 && nrhs > 0 && !X) return -5;
+  if (ldx < std::max(1, n)) return -6;
+  if (n > 0 && nrhs > 0 && !B) return -7;
+  if (ldb < std::max(1, n)) return -8;
+  if (nrhs > 0 && !d_beta) return -9;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!d_work || !aligned256(d_work)) return GBLA_ERR_WORKSPACE;
+  Carver c(d_work, work_bytes);
+  double* R = c.take<double>((size_t)std::max(n, 1) * std::max(nrhs, 1));
+  double* part = c.take<double>(residual_work_doubles(std::max(n, 1), std::min(std::max(nrhs, 1), 8)));
+  double* anorm = c.take<double>(1);
+  if (!c.ok) return GBLA_ERR_WORKSPACE;
+  if (nrhs == 0) return GBLA_OK;
+  if (n == 0) return cuda_status(cudaMemsetAsync(d_beta, 0, sizeof(double) * nrhs, s));
+  GBLA_TRY(launch_row_abs_sum_max(n, A, lda, part, anorm, s));
+  GBLA_TRY(launch_residual(n, nrhs, A, lda, X, ldx, B, ldb, R, n, part, s));
+  GBLA_TRY(launch_backward_error_finish(n, nrhs, R, n, X, ldx, anorm, d_beta, s));
+  return GBLA_OK;
+}
+
+// ---------------------------------------------------------------------------
+struct IrWork {
+  int* perm;
+  double* V;
+  int ldv;
+  double* w;
+  double* r;
+  double* H;
+  double* cs;
+  double* sn;
+  double* g;
+  double* st;  // GmresState {res, pad}
+  double* slots;
+  unsigned* counter;
+  unsigned* flags;
+  int* info;
+  double* anorm;
+  double* beta;
+  double* part;
+};
+
+static size_t ir_layout(Carver& c, int n, int m, IrWork* w) {
+  const int nn = std::max(n, 1);
+  const int ldv = ((nn + 31) / 32) * 32;
+  IrWork t;
+  t.perm = c.take<int>(nn);
+  t.ldv = ldv;
+  t.V = c.take<double>((size_t)ldv * (m + 1));
+  t.w = c.take<double>(nn);
+  t.r = c.take<double>(nn);
+  t.H = c.take<double>((size_t)(m + 1) * m);
+  t.cs = c.take<double>(m);
+  t.sn = c.take<double>(m);
+  t.g = c.take<double>(m + 1);
+  t.st = c.take<double>(2);
+  t.slots = c.take<double>(mgs_slots_doubles());
+  t.counter = c.take<unsigned>(1);
+  t.flags = c.take<unsigned>(trsv_flags_count(nn));
+  t.info = c.take<int>(1);
+  t.anorm = c.take<double>(1);
+  t.beta = c.take<double>(1);
+  t.part = c.take<double>(residual_work_doubles(nn, 1));
+  if (w) *w = t;
+  return c.off;
+}
+
+size_t gbla_gmresir_workspace(int n, int restart_m) {
+  if (n < 0 || restart_m < 1 || restart_m > 128) return 0;
+  Carver c(nullptr, 0);
+  return ir_layout(c, n, restart_m, nullptr);
+}
+
+// v <- M^{-1} v with M = P^t L U (FP32 factors, FP64 arithmetic); tmp: n doubles
+static cudaError_t apply_minv(int n, const float* F, int ldf, const int* perm, const double* src,
+                              double* dst, unsigned* flags, int* info, cudaStream_t s) {
+  cudaError_t e = launch_permute_rows(n, 1, perm, false, src, n, dst, n, s);
+  if (e != cudaSuccess) return e;
+  e = launch_trsv<float>(true, false, true, n, 1, F, ldf, dst, n, flags, info, s);
+  if (e != cudaSuccess) return e;
+  return launch_trsv<float>(false, false, false, n, 1, F, ldf, dst, n, flags, info, s);
+}
+
+static int read_scalar(double* host, const double* dev, const int* d_info, cudaStream_t s) {
+  int info = 0;
+  if (cudaMemcpyAsync(host, dev, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return GBLA_ERR_CUDA;
+  if (cudaMemcpyAsync(&info, d_info, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return GBLA_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return GBLA_ERR_CUDA;
+  return info == GBLA_INFO_TIMEOUT ? GBLA_ERR_TIMEOUT : GBLA_OK;
+}
+
+int gbla_gmresir_solve(int n, const double* A, int lda, const float* F, int ldf, const int* ipiv,
+                       const double* b, double* x, const gbla_gmresir_opts* opts,
+                       gbla_gmresir_stats* stats, void* d_work, size_t work_bytes,
+                       gbla_stream_t stream) {
+  if (n < 0) return -1;
+  if (n > 0 && !A) return -2;
+  if (lda < std::max(1, n)) return -3;
+  if (n > 0 && !F) return -4;
+  if (ldf < std::max(1, n)) return -5;
+  if (n > 0 && !ipiv) return -6;
+  if (n > 0 && !b) return -7;
+  if (n > 0 && !x) return -8;
+  if (!opts || opts->restart_m < 1 || opts->restart_m > 128 || opts->max_outer < 0 ||
+      !(opts->tol >= 0.0) || !(opts->inner_tol >= 0.0))
+    return -9;
+  if (!stats) return -10;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!d_work || !aligned256(d_work)) return GBLA_ERR_WORKSPACE;
+  const int m = opts->restart_m;
+  Carver c(d_work, work_bytes);
+  IrWork w;
+  ir_layout(c, n, m, &w);
+  if (!c.ok) return GBLA_ERR_WORKSPACE;
+  memset(stats, 0, sizeof(*stats));
+  if (n == 0) {
+    stats->converged = 1;
+    return GBLA_OK;
+  }
+  const DeviceProps& dp = device_props();
+  if (!dp.coop) return GBLA_ERR_DEVICE;
+  GBLA_TRY(cudaMemsetAsync(w.info, 0, sizeof(int), s));
+  GBLA_TRY(launch_ipiv_to_perm(n, ipiv, w.perm, s));
+  GBLA_TRY(launch_row_abs_sum_max(n, A, lda, w.part, w.anorm, s));
+  GBLA_TRY(apply_minv(n, F, ldf, w.perm, b, x, w.flags, w.info, s));
+  int rc = GBLA_OK;
+  for (int outer = 0;; ++outer) {
+    GBLA_TRY(launch_residual(n, 1, A, lda, x, n, b, n, w.r, n, w.part, s));
+    GBLA_TRY(launch_backward_error_finish(n, 1, w.r, n, x, n, w.anorm, w.beta, s));
+    double beta = 0.0;
+    rc = read_scalar(&beta, w.beta, w.info, s);
+    if (rc != GBLA_OK) return rc;
+    if (outer == 0) stats->beta0 = beta;
+    stats->beta = beta;
+    stats->outer = outer;
+    if (beta <= opts->tol) {
+      stats->converged = 1;
+      return GBLA_OK;
+    }
+    if (outer >= opts->max_outer) return GBLA_ERR_NOT_CONVERGED;
+    // z = M^{-1} r, v_0 = z / ||z||
+    GBLA_TRY(apply_minv(n, F, ldf, w.perm, w.r, w.w, w.flags, w.info, s));
+    GBLA_TRY(launch_mgs_step(n, -1, w.V, w.ldv, w.w, w.H, m + 1, w.cs, w.sn, w.g, w.st, w.slots,
+                             w.counter, w.info, s));
+    double beta_in = 0.0;
+    rc = read_scalar(&beta_in, w.st, w.info, s);
+    if (rc != GBLA_OK) return rc;
+    if (!(beta_in > 0.0)) {
+      stats->converged = 1;
+      return GBLA_OK;
+    }
+    int k = 0;
+    for (int j = 0; j < m; ++j) {
+      // w = M^{-1} A v_j
+      GBLA_TRY(launch_residual(n, 1, A, lda, w.V + (size_t)j * w.ldv, n, nullptr, n, w.w, n, w.part, s));
+      GBLA_TRY(apply_minv(n, F, ldf, w.perm, w.w, w.r, w.flags, w.info, s));
+      GBLA_TRY(launch_mgs_step(n, j, w.V, w.ldv, w.r, w.H, m + 1, w.cs, w.sn, w.g, w.st, w.slots,
+                               w.counter, w.info, s));
+      double res = 0.0;
+      rc = read_scalar(&res, w.st, w.info, s);
+      if (rc != GBLA_OK) return rc;
+      k = j + 1;
+      if (res <= opts->inner_tol * beta_in) break;
+    }
+    stats->inner += k;
+    GBLA_TRY(launch_gmres_update(n, k, w.V, w.ldv, w.H, m + 1, w.g, x, s));
+  }
+}
+
+}  // extern "C"

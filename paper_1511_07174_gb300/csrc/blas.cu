@@ -1,0 +1,469 @@
+// Level-3 pieces of the blocked LU (paper section 2, "delayed updating"):
+// row interchanges (laswp), the unit-lower triangular solve of the U row
+// block, the SIMT rank-k update (FP64 / FP32), the precision conversions that
+// feed the tensor-core update, and permutation helpers for the solves.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace gbla {
+
+// ----------------------------------------------------------------------------
+// laswp: apply the interchanges ipiv[k1..k2) (1-based global rows, in order)
+// to the columns [c0, c1) and [c2, c3). One thread per column.
+template <typename T>
+__global__ void laswp_kernel(T* __restrict__ A, int lda, int nrows, int c0, int c1, int c2, int c3,
+                             const int* __restrict__ ipiv, int k1, int k2) {
+  __shared__ int sp[512];
+  const int nk = k2 - k1;
+  for (int i = threadIdx.x; i < nk; i += blockDim.x) sp[i] = ipiv[k1 + i] - 1;
+  __syncthreads();
+  const int n1 = c1 - c0, n2 = c3 - c2;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n1 + n2) return;
+  const int col = t < n1 ? c0 + t : c2 + (t - n1);
+  T* a = A + (size_t)col * lda;
+  for (int i = 0; i < nk; ++i) {
+    const int k = k1 + i, p = sp[i];
+    if (p != k && p > k && p < nrows) {  // out-of-range pivots are ignored
+      T x = a[k];
+      a[k] = a[p];
+      a[p] = x;
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_laswp(T* A, int lda, int nrows, int c0, int c1, int c2, int c3, const int* ipiv,
+                         int k1, int k2, cudaStream_t s) {
+  if (c1 < c0) c1 = c0;
+  if (c3 < c2) c3 = c2;
+  const int ncols = (c1 - c0) + (c3 - c2);
+  if (ncols <= 0 || k2 <= k1) return cudaSuccess;
+  if (k2 - k1 > 512) return cudaErrorInvalidValue;
+  const int threads = 128;
+  laswp_kernel<T><<<(ncols + threads - 1) / threads, threads, 0, s>>>(A, lda, nrows, c0, c1, c2, c3,
+                                                                     ipiv, k1, k2);
+  return cudaGetLastError();
+}
+template cudaError_t launch_laswp<double>(double*, int, int, int, int, int, int, const int*, int,
+                                          int, cudaStream_t);
+template cudaError_t launch_laswp<float>(float*, int, int, int, int, int, int, const int*, int, int,
+                                         cudaStream_t);
+
+// ----------------------------------------------------------------------------
+// Low-precision conversion helpers (power-of-two sliver scaling).
+GBLA_DEVINL int sliver_exponent(float maxabs) {
+  if (!(maxabs > 0.0f)) return 0;
+  int e = 14 - ilogbf(maxabs);  // maxabs * 2^e in [2^14, 2^15)
+  return e > 100 ? 100 : (e < -100 ? -100 : e);
+}
+
+GBLA_DEVINL uint32_t f32_to_tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+template <int KIND>
+GBLA_DEVINL void store_lowp(void* base, size_t idx, float v) {
+  if constexpr (KIND == GBLA_PREC_BF16) {
+    reinterpret_cast<__nv_bfloat16*>(base)[idx] = __float2bfloat16_rn(v);
+  } else if constexpr (KIND == GBLA_PREC_FP16) {
+    reinterpret_cast<__half*>(base)[idx] = __float2half_rn(v);
+  } else {
+    reinterpret_cast<uint32_t*>(base)[idx] = f32_to_tf32_rna(v);
+  }
+}
+
+// ----------------------------------------------------------------------------
+// TRSM: B (w x N) <- L^{-1} B, L unit lower w x w. A warp owns 4 columns; lane
+// q*32+l of each column lives in lane l (rows r = lane + 32 q, q < 8, w <= 256).
+// Columns of L are staged through shared memory 32 at a time.
+constexpr int kTrsmCols = 32;  // columns per CTA (8 warps x 4)
+
+template <typename Ts, typename Tc, int OUT>
+__global__ void __launch_bounds__(256)
+    trsm_lunit_kernel(const Ts* __restrict__ L, int ldl, Ts* __restrict__ B, int ldb, int w, int N,
+                      void* __restrict__ outK, int ldk, int* __restrict__ outE) {
+  extern __shared__ unsigned char smraw[];
+  Tc* Ls = reinterpret_cast<Tc*>(smraw);  // [32][w]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int col0 = blockIdx.x * kTrsmCols + warp * 4;
+  Tc x[8][4];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int r = lane + 32 * q;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int col = col0 + c;
+      x[q][c] = (r < w && col < N) ? (Tc)B[r + (size_t)col * ldb] : (Tc)0;
+    }
+  }
+  for (int i0 = 0; i0 < w; i0 += 32) {
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < 32 * w; idx += blockDim.x) {
+      const int cc = idx / w, r = idx - cc * w, i = i0 + cc;
+      Ls[idx] = (i < w && r > i) ? (Tc)L[r + (size_t)i * ldl] : (Tc)0;
+    }
+    __syncthreads();
+    const int qi = i0 >> 5;
+    const int iend = min(32, w - i0);
+    for (int ii = 0; ii < iend; ++ii) {
+      Tc xi[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) xi[c] = (Tc)0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (q == qi) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) xi[c] = x[q][c];
+        }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) xi[c] = __shfl_sync(0xffffffffu, xi[c], ii);
+      const Tc* lcol = Ls + ii * w;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if (q >= qi) {
+          const int r = lane + 32 * q;
+          const Tc l = r < w ? lcol[r] : (Tc)0;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) x[q][c] = fma(-l, xi[c], x[q][c]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int col = col0 + c;
+    float mx = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int r = lane + 32 * q;
+      if (r < w && col < N) {
+        const Ts v = (Ts)x[q][c];
+        B[r + (size_t)col * ldb] = v;
+        if constexpr (OUT != 0) mx = fmaxf(mx, fabsf((float)v));
+      }
+    }
+    if constexpr (OUT != 0) {
+      mx = warp_max(mx);
+      const int e = (OUT == GBLA_PREC_TF32) ? 0 : sliver_exponent(mx);
+      if (col < N) {
+        if (lane == 0) outE[col] = e;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int r = lane + 32 * q;
+          if (r < w) store_lowp<OUT>(outK, (size_t)col * ldk + r, ldexpf((float)(Ts)x[q][c], e));
+        }
+      }
+    }
+  }
+}
+
+template <typename Ts, typename Tc>
+cudaError_t launch_trsm_lunit(const Ts* L, int ldl, Ts* B, int ldb, int w, int N, int out_kind,
+                              void* outK, int ldk, int* outE, cudaStream_t s) {
+  if (w <= 0 || N <= 0) return cudaSuccess;
+  if (w > 256) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)32 * w * sizeof(Tc);
+  const dim3 grid((N + kTrsmCols - 1) / kTrsmCols);
+  static bool attr[4] = {false, false, false, false};
+#define GBLA_TRSM_CASE(K, IDX)                                                                   \
+  {                                                                                            \
+    auto kfn = trsm_lunit_kernel<Ts, Tc, K>;                                                   \
+    if (!attr[IDX]) {                                                                          \
+      cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                                           (int)(64 * 1024 + 32 * 256 * 8));                   \
+      if (e != cudaSuccess) return e;                                                          \
+      attr[IDX] = true;                                                                        \
+    }                                                                                          \
+    kfn<<<grid, 256, smem, s>>>(L, ldl, B, ldb, w, N, outK, ldk, outE);                        \
+    break;                                                                                     \
+  }
+  switch (out_kind) {
+    case 0: GBLA_TRSM_CASE(0, 0)
+    case GBLA_PREC_BF16: GBLA_TRSM_CASE(GBLA_PREC_BF16, 1)
+    case GBLA_PREC_FP16: GBLA_TRSM_CASE(GBLA_PREC_FP16, 2)
+    case GBLA_PREC_TF32: GBLA_TRSM_CASE(GBLA_PREC_TF32, 3)
+    default: return cudaErrorInvalidValue;
+  }
+#undef GBLA_TRSM_CASE
+  return cudaGetLastError();
+}
+template cudaError_t launch_trsm_lunit<double, double>(const double*, int, double*, int, int, int,
+                                                       int, void*, int, int*, cudaStream_t);
+template cudaError_t launch_trsm_lunit<float, float>(const float*, int, float*, int, int, int, int,
+                                                     void*, int, int*, cudaStream_t);
+template cudaError_t launch_trsm_lunit<float, double>(const float*, int, float*, int, int, int,
+                                                      int, void*, int, int*, cudaStream_t);
+
+// ----------------------------------------------------------------------------
+// SIMT GEMM: C = alpha * A * op(B) + beta * C. Thread (tx, ty) owns rows
+// tx + i*(BM/TM) and columns ty + j*(BN/TN) of the tile, so that the lanes of
+// a warp touch consecutive rows of column-major C.
+template <typename T, int BM, int BN, int BK, int TM, int TN, bool TRANSB, bool LOWER>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+    gemm_simt_kernel(int M, int N, int K, T alpha, const T* __restrict__ A, int lda,
+                     const T* __restrict__ B, int ldb, T beta, T* __restrict__ C, int ldc) {
+  constexpr int NT = (BM / TM) * (BN / TN);
+  constexpr int RX = BM / TM, RY = BN / TN;
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BN + 1];
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  if (LOWER && m0 + BM - 1 < n0) return;  // tile strictly above the diagonal
+  const int tid = threadIdx.x;
+  const int tx = tid % RX, ty = tid / RX;
+  T acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = (T)0;
+  for (int k0 = 0; k0 < K; k0 += BK) {
+    for (int idx = tid; idx < BM * BK; idx += NT) {
+      const int mm = idx % BM, kk = idx / BM;
+      const int m = m0 + mm, k = k0 + kk;
+      As[kk][mm] = (m < M && k < K) ? A[m + (size_t)k * lda] : (T)0;
+    }
+    for (int idx = tid; idx < BN * BK; idx += NT) {
+      int nn, kk;
+      if (TRANSB) {
+        nn = idx % BN;
+        kk = idx / BN;
+      } else {
+        kk = idx % BK;
+        nn = idx / BK;
+      }
+      const int nidx = n0 + nn, k = k0 + kk;
+      T v = (T)0;
+      if (nidx < N && k < K) v = TRANSB ? B[nidx + (size_t)k * ldb] : B[k + (size_t)nidx * ldb];
+      Bs[kk][nn] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T a[TM], b[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][tx + i * RX];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][ty + j * RY];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < TN; ++j) {
+    const int n = n0 + ty + j * RY;
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+      const int m = m0 + tx + i * RX;
+      if (m < M && n < N && (!LOWER || m >= n)) {
+        T* c = C + m + (size_t)n * ldc;
+        *c = (beta == (T)0) ? alpha * acc[i][j] : fma(alpha, acc[i][j], beta * *c);
+      }
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_gemm_simt(int M, int N, int K, T alpha, const T* A, int lda, const T* B,
+                             int ldb, bool transB, T beta, T* C, int ldc, bool lower,
+                             cudaStream_t s) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if constexpr (sizeof(T) == 8) {
+    constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4;
+    dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN);
+    if (transB) {
+      if (lower)
+        gemm_simt_kernel<T, BM, BN, BK, TM, TN, true, true><<<grid, 256, 0, s>>>(
+            M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+      else
+        gemm_simt_kernel<T, BM, BN, BK, TM, TN, true, false><<<grid, 256, 0, s>>>(
+            M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    } else {
+      gemm_simt_kernel<T, BM, BN, BK, TM, TN, false, false><<<grid, 256, 0, s>>>(
+          M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    }
+  } else {
+    constexpr int BM = 128, BN = 128, BK = 8, TM = 8, TN = 8;
+    dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN);
+    if (transB) {
+      if (lower)
+        gemm_simt_kernel<T, BM, BN, BK, TM, TN, true, true><<<grid, 256, 0, s>>>(
+            M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+      else
+        gemm_simt_kernel<T, BM, BN, BK, TM, TN, true, false><<<grid, 256, 0, s>>>(
+            M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    } else {
+      gemm_simt_kernel<T, BM, BN, BK, TM, TN, false, false><<<grid, 256, 0, s>>>(
+          M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    }
+  }
+  return cudaGetLastError();
+}
+template cudaError_t launch_gemm_simt<double>(int, int, int, double, const double*, int,
+                                              const double*, int, bool, double, double*, int,
+                                              bool, cudaStream_t);
+template cudaError_t launch_gemm_simt<float>(int, int, int, float, const float*, int, const float*,
+                                             int, bool, float, float*, int, bool, cudaStream_t);
+
+// ----------------------------------------------------------------------------
+// L21 (FP32, M x K column-major) -> K-major low-precision rows with one
+// power-of-two exponent per row. CTA: 32 rows; shared-memory transpose.
+template <int KIND>
+__global__ void __launch_bounds__(256)
+    convert_rows_kernel(const float* __restrict__ F, int ldf, int M, int K, void* __restrict__ outK,
+                        int ldk, int* __restrict__ outE) {
+  __shared__ float tile[64][33];
+  __shared__ float wmax[8][32];
+  __shared__ int es[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int m0 = blockIdx.x * 32;
+  const int m = m0 + lane;
+  float mx = 0.0f;
+  if (m < M)
+    for (int k = warp; k < K; k += 8) mx = fmaxf(mx, fabsf(F[m + (size_t)k * ldf]));
+  wmax[warp][lane] = mx;
+  __syncthreads();
+  if (warp == 0) {
+    float v = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v = fmaxf(v, wmax[q][lane]);
+    const int e = (KIND == GBLA_PREC_TF32) ? 0 : sliver_exponent(v);
+    es[lane] = e;
+    if (m < M) outE[m] = e;
+  }
+  __syncthreads();
+  for (int k0 = 0; k0 < K; k0 += 64) {
+    for (int idx = threadIdx.x; idx < 64 * 32; idx += 256) {
+      const int kk = idx >> 5, mm = idx & 31;
+      const int mr = m0 + mm, k = k0 + kk;
+      tile[kk][mm] = (mr < M && k < K) ? F[mr + (size_t)k * ldf] : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int mm = warp * 4 + r, mr = m0 + mm;
+      if (mr < M) {
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          const int kk = lane * 2 + t, k = k0 + kk;
+          if (k < K) store_lowp<KIND>(outK, (size_t)mr * ldk + k, ldexpf(tile[kk][mm], es[mm]));
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_convert_rows(const float* F, int ldf, int M, int K, int kind, void* outK,
+                                int ldk, int* outE, cudaStream_t s) {
+  if (M <= 0 || K <= 0) return cudaSuccess;
+  dim3 grid((M + 31) / 32);
+  switch (kind) {
+    case GBLA_PREC_BF16:
+      convert_rows_kernel<GBLA_PREC_BF16><<<grid, 256, 0, s>>>(F, ldf, M, K, outK, ldk, outE);
+      break;
+    case GBLA_PREC_FP16:
+      convert_rows_kernel<GBLA_PREC_FP16><<<grid, 256, 0, s>>>(F, ldf, M, K, outK, ldk, outE);
+      break;
+    case GBLA_PREC_TF32:
+      convert_rows_kernel<GBLA_PREC_TF32><<<grid, 256, 0, s>>>(F, ldf, M, K, outK, ldk, outE);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+__global__ void copy_d2f_kernel(const double* __restrict__ A, int lda, float* __restrict__ F,
+                                int ldf, int m, int n) {
+  const int col = blockIdx.y;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x)
+    F[r + (size_t)col * ldf] = (float)A[r + (size_t)col * lda];
+}
+
+cudaError_t launch_copy_d2f(const double* A, int lda, float* F, int ldf, int m, int n,
+                            cudaStream_t s) {
+  if (m <= 0 || n <= 0) return cudaSuccess;
+  int bx = (m + 255) / 256;
+  if (bx > 16) bx = 16;
+  for (int c0 = 0; c0 < n; c0 += 65535) {
+    const int nc = n - c0 < 65535 ? n - c0 : 65535;
+    copy_d2f_kernel<<<dim3(bx, nc), 256, 0, s>>>(A + (size_t)c0 * lda, lda, F + (size_t)c0 * ldf,
+                                                 ldf, m, nc);
+  }
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// perm from sequential interchanges: (P v)[i] = v[perm[i]]. One thread applies
+// the n swaps in order on a shared-memory (or, for very large n, global) array.
+__global__ void ipiv_to_perm_kernel(int n, const int* __restrict__ ipiv, int* __restrict__ perm,
+                                    int use_smem) {
+  extern __shared__ int sp[];
+  int* p = use_smem ? sp : perm;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = i;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int j = 0; j < n; ++j) {
+      const int k = ipiv[j] - 1;
+      if (k != j && k > j && k < n) {  // out-of-range pivots are ignored
+        const int t = p[j];
+        p[j] = p[k];
+        p[k] = t;
+      }
+    }
+  }
+  __syncthreads();
+  if (use_smem)
+    for (int i = threadIdx.x; i < n; i += blockDim.x) perm[i] = p[i];
+}
+
+cudaError_t launch_ipiv_to_perm(int n, const int* ipiv, int* perm, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const DeviceProps& dp = device_props();
+  const size_t bytes = (size_t)n * sizeof(int);
+  const int use_smem = bytes <= dp.smem_optin ? 1 : 0;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(ipiv_to_perm_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)dp.smem_optin);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  ipiv_to_perm_kernel<<<1, 1024, use_smem ? bytes : 0, s>>>(n, ipiv, perm, use_smem);
+  return cudaGetLastError();
+}
+
+__global__ void permute_rows_kernel(int n, int nrhs, const int* __restrict__ perm, int inverse,
+                                    const double* __restrict__ src, int lds,
+                                    double* __restrict__ dst, int ldd) {
+  const int c = blockIdx.y;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int p = perm[i];
+    if (inverse)
+      dst[p + (size_t)c * ldd] = src[i + (size_t)c * lds];
+    else
+      dst[i + (size_t)c * ldd] = src[p + (size_t)c * lds];
+  }
+}
+
+cudaError_t launch_permute_rows(int n, int nrhs, const int* perm, bool inverse, const double* src,
+                                int lds, double* dst, int ldd, cudaStream_t s) {
+  if (n <= 0 || nrhs <= 0) return cudaSuccess;
+  int bx = (n + 255) / 256;
+  if (bx > 1024) bx = 1024;
+  permute_rows_kernel<<<dim3(bx, nrhs), 256, 0, s>>>(n, nrhs, perm, inverse ? 1 : 0, src, lds, dst,
+                                                     ldd);
+  return cudaGetLastError();
+}
+
+}  // namespace gbla

@@ -1,0 +1,340 @@
+// Trailing-matrix update of the mixed-precision LU on the 5th-generation tensor
+// cores (paper section 2: the rank-k "delayed update" A22 -= L21 U12).
+//
+// One CTA computes a 128 x 128 tile D = L21_tile * U12_tile with tcgen05.mma
+// (cta_group::1, M = 128, N = 128, K = 16 per instruction for 16-bit operands,
+// 8 for TF32), FP32 accumulator in tensor memory (128 TMEM columns). Operands
+// are K-major copies (one row of K elements per matrix row), loaded by TMA
+// with 128-byte swizzle into a 4-stage shared-memory ring guarded by mbarriers:
+//   warp 0 lane 0  -- TMA producer
+//   warp 1 lane 0  -- MMA issuer (tcgen05.commit frees a stage / signals done)
+//   warps 0..3     -- epilogue: tcgen05.ld of the warp's 32 TMEM lanes, then
+//                     C[row, col] -= D * 2^-eA[row] * 2^-eB[col] on the FP32
+//                     working matrix (column-major; a warp covers 32
+//                     consecutive rows, so every access is one 128-byte line).
+// Every mbarrier wait is bounded; a wait that gives up records
+// GBLA_INFO_TIMEOUT, skips the epilogue writes, drains the copies it issued and
+// frees its tensor memory before returning.
+#include <cuda.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace gbla {
+
+constexpr int kTcBM = 128, kTcBN = 128, kTcStages = 4;
+constexpr int kTcStageBytes = 128 * 128;  // one operand tile: 128 rows x 128 bytes
+constexpr int kTcSmemBytes = 2 * kTcStages * kTcStageBytes + 1024 /*align*/ + 256 /*barriers*/;
+
+GBLA_DEVINL uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+GBLA_DEVINL void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+GBLA_DEVINL void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+GBLA_DEVINL bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+GBLA_DEVINL bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = gbla_now_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (gbla_now_ns() - t0 > limit_ns) return false;
+  }
+  return true;
+}
+
+GBLA_DEVINL void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes, 8-row groups 1024 bytes apart (stride byte offset); the leading
+// byte offset is unused for swizzled K-major layouts (set to 1).
+GBLA_DEVINL uint64_t make_sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor: FP32 accumulator, A/B format (0 FP16, 1 BF16,
+// 2 TF32), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t make_idesc(uint32_t ab_fmt, int M, int N) {
+  return (1u << 4) | (ab_fmt << 7) | (ab_fmt << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+template <int KIND>
+GBLA_DEVINL void mma_issue(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                           uint32_t accumulate) {
+  if constexpr (KIND == GBLA_PREC_TF32) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+  }
+}
+
+GBLA_DEVINL void mma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+GBLA_DEVINL void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+      "%30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+        "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+        "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// 2^e for |e| <= 126, built from the exponent field (exact).
+GBLA_DEVINL float pow2f(int e) { return __int_as_float((127 + e) << 23); }
+
+struct TcArgs {
+  int M, N, K;
+  float* C;
+  int ldc;
+  const int* eA;
+  const int* eB;
+  int* info;
+  uint64_t wait_ns;
+};
+
+template <int KIND>
+__global__ void __launch_bounds__(128, 1)
+    gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   TcArgs args) {
+  extern __shared__ unsigned char smraw[];
+  const uint32_t raw = smem_u32(smraw);
+  const uint32_t sbase = (raw + 1023u) & ~1023u;
+  unsigned char* sm = smraw + (sbase - raw);
+  const uint32_t sA = sbase;
+  const uint32_t sB = sbase + kTcStages * kTcStageBytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + 2 * kTcStages * kTcStageBytes);
+  const uint32_t bar_full = smem_u32(bars);
+  const uint32_t bar_empty = bar_full + 8 * kTcStages;
+  const uint32_t bar_done = bar_full + 16 * kTcStages;
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * kTcStages + 1);
+  int* s_fail = reinterpret_cast<int*>(tmem_holder + 1);
+  int* s_issued = s_fail + 1;
+
+  constexpr int kElem = (KIND == GBLA_PREC_TF32) ? 4 : 2;
+  constexpr int kBK = 128 / kElem;  // elements per 128-byte row
+  constexpr uint32_t kIdesc =
+      make_idesc(KIND == GBLA_PREC_TF32 ? 2u : (KIND == GBLA_PREC_BF16 ? 1u : 0u), kTcBM, kTcBN);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * kTcBM, n0 = blockIdx.y * kTcBN;
+  const int KB = (args.K + kBK - 1) / kBK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kTcStages; ++s) {
+      mbar_init(bar_full + 8 * s, 1);
+      mbar_init(bar_empty + 8 * s, 1);
+    }
+    mbar_init(bar_done, 1);
+    *s_fail = 0;
+    *s_issued = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_holder)),
+                 "r"(kTcBN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_holder;
+
+  if (warp == 0 && lane == 0) {
+    int kb = 0;
+    for (; kb < KB; ++kb) {
+      const int s = kb % kTcStages;
+      const uint32_t ph = (uint32_t)((kb / kTcStages) & 1);
+      if (!mbar_wait_bounded(bar_empty + 8 * s, ph ^ 1u, args.wait_ns)) {
+        atomicExch(s_fail, 1);
+        break;
+      }
+      mbar_expect_tx(bar_full + 8 * s, 2 * kTcStageBytes);
+      tma_load_2d(sA + s * kTcStageBytes, &tmA, kb * kBK, m0, bar_full + 8 * s);
+      tma_load_2d(sB + s * kTcStageBytes, &tmB, kb * kBK, n0, bar_full + 8 * s);
+    }
+    *s_issued = kb;
+  } else if (warp == 1 && lane == 0) {
+    for (int kb = 0; kb < KB; ++kb) {
+      const int s = kb % kTcStages;
+      const uint32_t ph = (uint32_t)((kb / kTcStages) & 1);
+      if (!mbar_wait_bounded(bar_full + 8 * s, ph, args.wait_ns)) {
+        atomicExch(s_fail, 1);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const uint64_t ad = make_sdesc(sA + s * kTcStageBytes + kk * 32);
+        const uint64_t bd = make_sdesc(sB + s * kTcStageBytes + kk * 32);
+        mma_issue<KIND>(tmem, ad, bd, kIdesc, (kb > 0 || kk > 0) ? 1u : 0u);
+      }
+      mma_commit(bar_empty + 8 * s);
+    }
+    mma_commit(bar_done);
+  }
+  __syncwarp();
+
+  if (!mbar_wait_bounded(bar_done, 0, args.wait_ns)) atomicExch(s_fail, 1);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  __syncthreads();
+  const bool fail = *(volatile int*)s_fail != 0;  // uniform across the CTA
+  if (fail) {
+    if (threadIdx.x == 0) {
+      gbla_flag_timeout(args.info);
+      // drain TMA copies that were issued but never consumed
+      const int issued = *(volatile int*)s_issued;
+      for (int kb = (issued > kTcStages ? issued - kTcStages : 0); kb < issued; ++kb)
+        mbar_wait_bounded(bar_full + 8 * (kb % kTcStages), (uint32_t)((kb / kTcStages) & 1),
+                          args.wait_ns);
+    }
+  } else {
+    const int row = m0 + warp * 32 + lane;
+    const bool rok = row < args.M;
+    const float sa = (rok && args.eA) ? pow2f(-args.eA[row]) : 1.0f;
+    float* crow = args.C + row;
+#pragma unroll 1
+    for (int cb = 0; cb < kTcBN; cb += 32) {
+      uint32_t v[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
+      if (rok) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int col = n0 + cb + j;
+          if (col < args.N) {
+            const float sb = args.eB ? pow2f(-__ldg(args.eB + col)) : 1.0f;
+            float* c = crow + (size_t)col * args.ldc;
+            *c = *c - (__uint_as_float(v[j]) * sa) * sb;
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcBN));
+  }
+}
+
+// ---------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn get_encode() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+static bool encode_kmajor(CUtensorMap* map, int kind, const void* ptr, int K, int rows, int ld) {
+  EncodeTiledFn enc = get_encode();
+  if (!enc) return false;
+  const int elem = kind == GBLA_PREC_TF32 ? 4 : 2;
+  CUtensorMapDataType dt = kind == GBLA_PREC_TF32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                           : kind == GBLA_PREC_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                    : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  cuuint64_t gdim[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  cuuint64_t gstride[1] = {(cuuint64_t)ld * elem};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / elem), 128u};
+  cuuint32_t estr[2] = {1u, 1u};
+  CUresult r = enc(map, dt, 2, const_cast<void*>(ptr), gdim, gstride, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+cudaError_t launch_gemm_tc(int kind, int M, int N, int K, const void* Ak, int ldak, const void* Bk,
+                           int ldbk, const int* eA, const int* eB, float* C, int ldc, int* info,
+                           cudaStream_t s) {
+  if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+  const int elem = kind == GBLA_PREC_TF32 ? 4 : 2;
+  if (((size_t)ldak * elem) % 16 != 0 || ((size_t)ldbk * elem) % 16 != 0) return cudaErrorInvalidValue;
+  if ((reinterpret_cast<uintptr_t>(Ak) & 15) || (reinterpret_cast<uintptr_t>(Bk) & 15))
+    return cudaErrorInvalidValue;
+  CUtensorMap ta, tb;
+  if (!encode_kmajor(&ta, kind, Ak, K, M, ldak)) return cudaErrorInvalidValue;
+  if (!encode_kmajor(&tb, kind, Bk, K, N, ldbk)) return cudaErrorInvalidValue;
+  TcArgs a{M, N, K, C, ldc, eA, eB, info, wait_timeout_ns()};
+  const dim3 grid((M + kTcBM - 1) / kTcBM, (N + kTcBN - 1) / kTcBN);
+  static bool attr[5] = {false, false, false, false, false};
+  switch (kind) {
+#define GBLA_TC_CASE(K)                                                                         \
+  case K: {                                                                                   \
+    if (!attr[K]) {                                                                           \
+      cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<K>,                                 \
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,       \
+                                           kTcSmemBytes);                                     \
+      if (e != cudaSuccess) return e;                                                         \
+      attr[K] = true;                                                                         \
+    }                                                                                         \
+    gemm_tc_kernel<K><<<grid, 128, kTcSmemBytes, s>>>(ta, tb, a);                              \
+    break;                                                                                    \
+  }
+    GBLA_TC_CASE(GBLA_PREC_TF32)
+    GBLA_TC_CASE(GBLA_PREC_BF16)
+    GBLA_TC_CASE(GBLA_PREC_FP16)
+#undef GBLA_TC_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace gbla

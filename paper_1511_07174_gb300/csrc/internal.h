@@ -1,0 +1,126 @@
+// Host-side declarations shared by the translation units of libgbla (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/gbla.h"
+
+namespace gbla {
+
+// ---- process-wide settings ------------------------------------------------
+uint64_t wait_timeout_ns();
+
+struct DeviceProps {
+  int device = -1;
+  int num_sms = 0;
+  int coop = 0;
+  size_t smem_optin = 0;
+};
+const DeviceProps& device_props();
+
+// ---- workspace carving -----------------------------------------------------
+struct Carver {
+  char* base;
+  size_t cap;
+  size_t off = 0;
+  bool ok = true;
+  Carver(void* b, size_t c) : base(static_cast<char*>(b)), cap(c) {}
+  template <typename T>
+  T* take(size_t count) {
+    size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+    if (base == nullptr) {  // sizing pass
+      off += bytes;
+      return nullptr;
+    }
+    if (off + bytes > cap) {
+      ok = false;
+      return nullptr;
+    }
+    T* p = reinterpret_cast<T*>(base + off);
+    off += bytes;
+    return p;
+  }
+};
+
+// ---- kernel launchers (all stream-ordered; return cudaError_t) -------------
+constexpr int kPanelWidth = 32;  // inner panel width handled by the cooperative kernel
+constexpr int kPanelSlotW = 72;  // doubles per published candidate slot
+
+// Workspace for one panel launch: 2 * (num_sms + 1) slots + counters.
+size_t panel_slots_doubles();
+
+template <typename Ts>
+cudaError_t launch_panel(Ts* A, int lda, int m, int w, int row0, int* ipiv, int* info,
+                         double* slots, unsigned* counter, cudaStream_t s);
+
+// Interchanges ipiv[k1..k2) on columns [c0,c1) u [c2,c3); rows outside
+// [k, nrows) named by a pivot are ignored (defensive: never index out of A).
+template <typename T>
+cudaError_t launch_laswp(T* A, int lda, int nrows, int c0, int c1, int c2, int c3, const int* ipiv,
+                         int k1, int k2, cudaStream_t s);
+
+// B (w x N, ldb) <- L^{-1} B with L unit lower (w x w, ldl). Tc: arithmetic type.
+// out_kind: 0 none, GBLA_PREC_BF16/FP16/TF32 -> also write a K-major copy of
+// the result (column j at outK + j*ldk, 2- or 4-byte elements) with one
+// power-of-two scale exponent per column (outE[j]; 0 for TF32).
+template <typename Ts, typename Tc>
+cudaError_t launch_trsm_lunit(const Ts* L, int ldl, Ts* B, int ldb, int w, int N, int out_kind,
+                              void* outK, int ldk, int* outE, cudaStream_t s);
+
+// C = alpha * A * op(B) + beta * C (column-major). transB: op(B) = B^t with B
+// stored N x K. lower: only elements with row >= col are written.
+template <typename T>
+cudaError_t launch_gemm_simt(int M, int N, int K, T alpha, const T* A, int lda, const T* B,
+                             int ldb, bool transB, T beta, T* C, int ldc, bool lower,
+                             cudaStream_t s);
+
+// K-major low-precision copy of an FP32 M x K block (rows scaled per row).
+cudaError_t launch_convert_rows(const float* F, int ldf, int M, int K, int kind, void* outK,
+                                int ldk, int* outE, cudaStream_t s);
+
+cudaError_t launch_copy_d2f(const double* A, int lda, float* F, int ldf, int m, int n,
+                            cudaStream_t s);
+
+// tcgen05 trailing update: C (M x N FP32) -= 2^-eA[i] * (A_k B_k^t)[i,j] * 2^-eB[j].
+// A_k: M rows of K elements (row stride ldak elements), B_k: N rows of K (ldbk).
+cudaError_t launch_gemm_tc(int kind, int M, int N, int K, const void* Ak, int ldak,
+                           const void* Bk, int ldbk, const int* eA, const int* eB, float* C,
+                           int ldc, int* info, cudaStream_t s);
+
+// ---- triangular solves ------------------------------------------------------
+// uplo_lower: the stored triangle; trans: solve with its transpose; unit: unit diagonal.
+// X (n x nrhs, ldx) FP64 is overwritten in place. flags: >= ceil(n/64)+1 uints.
+template <typename Ts>
+cudaError_t launch_trsv(bool lower, bool trans, bool unit, int n, int nrhs, const Ts* T, int ldt,
+                        double* X, int ldx, unsigned* flags, int* info, cudaStream_t s);
+size_t trsv_flags_count(int n);
+
+cudaError_t launch_ipiv_to_perm(int n, const int* ipiv, int* perm, cudaStream_t s);
+// dst[i, c] = src[perm[i], c] (forward) or dst[perm[i], c] = src[i, c] (inverse)
+cudaError_t launch_permute_rows(int n, int nrhs, const int* perm, bool inverse, const double* src,
+                                int lds, double* dst, int ldd, cudaStream_t s);
+
+// ---- residual / norms / GMRES -----------------------------------------------
+// R = B - A X (or R = A X when B == nullptr); partial sums in work (chunks x n x nrhs doubles).
+size_t residual_work_doubles(int n, int nrhs);
+cudaError_t launch_residual(int n, int nrhs, const double* A, int lda, const double* X, int ldx,
+                            const double* B, int ldb, double* R, int ldr, double* work,
+                            cudaStream_t s);
+// anorm[0] = max_i sum_j |a_ij|; work >= residual_work_doubles(n, 1)
+cudaError_t launch_row_abs_sum_max(int n, const double* A, int lda, double* work, double* anorm,
+                                   cudaStream_t s);
+// beta[c] = max|R(:,c)| / (anorm * max|X(:,c)|)
+cudaError_t launch_backward_error_finish(int n, int nrhs, const double* R, int ldr,
+                                         const double* X, int ldx, const double* anorm,
+                                         double* beta, cudaStream_t s);
+
+// GMRES pieces (krylov.cu). st points to a device GmresState {double res, pad}.
+size_t mgs_slots_doubles();
+cudaError_t launch_mgs_step(int n, int j, double* V, int ldv, const double* w, double* H, int ldh,
+                            double* cs, double* sn, double* g, void* st, double* slots,
+                            unsigned* counter, int* info, cudaStream_t s);
+cudaError_t launch_gmres_update(int n, int k, const double* V, int ldv, const double* H, int ldh,
+                                const double* g, double* x, cudaStream_t s);
+
+}  // namespace gbla

@@ -1,0 +1,190 @@
+// Forward and back substitution (paper section 2: L y = b, U x = y; and the
+// transposed systems used by the gradient and by Cholesky's L^t x = y).
+//
+// The n rows are cut into 64-row blocks. Each CTA draws a ticket (atomic, in
+// start order) that names the block it solves, so a CTA only ever waits on
+// blocks owned by CTAs that started before it. For its block b it streams the
+// 64 x 64 tiles M(b, q) of every earlier block q in solve order (coalesced
+// loads into shared memory in either orientation), waits (bounded) for block
+// q's flag, and accumulates M(b, q) x_q; then it solves its diagonal block
+// in shared memory (one warp per right-hand side, lanes own rows), writes
+// x_b and releases its flag. Arithmetic is FP64 whatever the storage type of
+// the triangular factor (FP64 or FP32).
+#include "common.cuh"
+#include "internal.h"
+
+namespace gbla {
+
+constexpr int kTsBS = 64;
+constexpr int kTsNR = 16;
+
+size_t trsv_flags_count(int n) { return (size_t)((n + kTsBS - 1) / kTsBS) + 1; }
+
+template <typename Ts, bool LOWER, bool TRANS, bool UNIT>
+__global__ void __launch_bounds__(256)
+    trsv_chain_kernel(int n, int nrhs, const Ts* __restrict__ T, int ldt, double* X, int ldx,
+                      unsigned* flags, int* info, uint64_t wait_ns) {
+  constexpr bool FWD = (LOWER != TRANS);
+  __shared__ double tile[kTsBS][kTsBS + 1];
+  __shared__ double xq[kTsBS][kTsNR];
+  __shared__ int s_t, s_abort;
+  const int tid = threadIdx.x;
+  const int nblk = (n + kTsBS - 1) / kTsBS;
+  if (tid == 0) {
+    s_t = (int)atomicAdd(&flags[nblk], 1u);
+    s_abort = 0;
+  }
+  __syncthreads();
+  const int t_ord = s_t;
+  if (t_ord >= nblk) return;
+  const int b = FWD ? t_ord : nblk - 1 - t_ord;
+  const int r0 = b * kTsBS;
+  const int nr = min(kTsBS, n - r0);
+  const int r = tid & 63, g = tid >> 6;
+
+  auto load_tile = [&](int c0, int nc) {
+    for (int idx = tid; idx < kTsBS * kTsBS; idx += blockDim.x) {
+      int rr, jj;
+      if (!TRANS) {
+        rr = idx & 63;
+        jj = idx >> 6;
+      } else {
+        jj = idx & 63;
+        rr = idx >> 6;
+      }
+      double v = 0.0;
+      if (rr < nr && jj < nc)
+        v = TRANS ? (double)T[(c0 + jj) + (size_t)(r0 + rr) * ldt]
+                  : (double)T[(r0 + rr) + (size_t)(c0 + jj) * ldt];
+      tile[rr][jj] = v;
+    }
+  };
+
+  double acc[kTsNR];
+#pragma unroll
+  for (int c = 0; c < kTsNR; ++c) acc[c] = 0.0;
+
+  for (int st = 0; st < t_ord; ++st) {
+    const int q = FWD ? st : nblk - 1 - st;
+    const int c0 = q * kTsBS;
+    const int nc = min(kTsBS, n - c0);
+    __syncthreads();
+    load_tile(c0, nc);
+    if (tid == 0) {
+      if (!gbla_wait_geq(&flags[q], 1u, wait_ns)) {
+        gbla_flag_timeout(info);
+        s_abort = 1;
+      }
+      __threadfence();
+    }
+    __syncthreads();
+    if (s_abort) return;
+    for (int idx = tid; idx < kTsBS * nrhs; idx += blockDim.x) {
+      const int jj = idx & 63, c = idx >> 6;
+      xq[jj][c] = jj < nc ? __ldcg(&X[(c0 + jj) + (size_t)c * ldx]) : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int jj = g * 16; jj < g * 16 + 16; ++jj) {
+      const double tv = tile[r][jj];
+#pragma unroll
+      for (int c = 0; c < kTsNR; ++c)
+        if (c < nrhs) acc[c] = fma(tv, xq[jj][c], acc[c]);
+    }
+  }
+  // reduce the four partial sums of each row; the right-hand side of block b
+  __syncthreads();
+  double* part = &tile[0][0];
+#pragma unroll
+  for (int c = 0; c < kTsNR; ++c)
+    if (c < nrhs) part[(g * kTsBS + r) * kTsNR + c] = acc[c];
+  __syncthreads();
+  for (int idx = tid; idx < kTsBS * nrhs; idx += blockDim.x) {
+    const int rr = idx & 63, c = idx >> 6;
+    double v = 0.0;
+    if (rr < nr) {
+      const double sum = (part[(0 * kTsBS + rr) * kTsNR + c] + part[(1 * kTsBS + rr) * kTsNR + c]) +
+                         (part[(2 * kTsBS + rr) * kTsNR + c] + part[(3 * kTsBS + rr) * kTsNR + c]);
+      v = __ldcg(&X[(r0 + rr) + (size_t)c * ldx]) - sum;
+    }
+    xq[rr][c] = v;
+  }
+  __syncthreads();
+  load_tile(r0, nr);  // diagonal block
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31;
+  for (int c = warp; c < nrhs; c += (int)(blockDim.x >> 5)) {
+    double y0 = xq[lane][c], y1 = xq[lane + 32][c];
+    if (FWD) {
+      for (int i = 0; i < nr; ++i) {
+        double xi = __shfl_sync(0xffffffffu, i < 32 ? y0 : y1, i & 31);
+        if (!UNIT) xi = xi / tile[i][i];
+        if (lane == (i & 31)) {
+          if (i < 32) y0 = xi;
+          else y1 = xi;
+        }
+        if (lane > i) y0 = fma(-tile[lane][i], xi, y0);
+        if (lane + 32 > i) y1 = fma(-tile[lane + 32][i], xi, y1);
+      }
+    } else {
+      for (int i = nr - 1; i >= 0; --i) {
+        double xi = __shfl_sync(0xffffffffu, i < 32 ? y0 : y1, i & 31);
+        if (!UNIT) xi = xi / tile[i][i];
+        if (lane == (i & 31)) {
+          if (i < 32) y0 = xi;
+          else y1 = xi;
+        }
+        if (lane < i) y0 = fma(-tile[lane][i], xi, y0);
+        if (lane + 32 < i) y1 = fma(-tile[lane + 32][i], xi, y1);
+      }
+    }
+    xq[lane][c] = y0;
+    xq[lane + 32][c] = y1;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < kTsBS * nrhs; idx += blockDim.x) {
+    const int rr = idx & 63, c = idx >> 6;
+    if (rr < nr) X[(r0 + rr) + (size_t)c * ldx] = xq[rr][c];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    st_release_u32(&flags[b], 1u);
+  }
+}
+
+template <typename Ts>
+cudaError_t launch_trsv(bool lower, bool trans, bool unit, int n, int nrhs, const Ts* T, int ldt,
+                        double* X, int ldx, unsigned* flags, int* info, cudaStream_t s) {
+  if (n <= 0 || nrhs <= 0) return cudaSuccess;
+  const int nblk = (n + kTsBS - 1) / kTsBS;
+  const uint64_t wait_ns = wait_timeout_ns();
+  for (int c0 = 0; c0 < nrhs; c0 += kTsNR) {
+    const int nc = nrhs - c0 < kTsNR ? nrhs - c0 : kTsNR;
+    cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(unsigned) * (size_t)(nblk + 1), s);
+    if (e != cudaSuccess) return e;
+    double* Xc = X + (size_t)c0 * ldx;
+#define GBLA_TRSV(LW, TR, UN)                                                                  \
+  trsv_chain_kernel<Ts, LW, TR, UN><<<nblk, 256, 0, s>>>(n, nc, T, ldt, Xc, ldx, flags, info, \
+                                                         wait_ns)
+    if (lower && !trans && unit) GBLA_TRSV(true, false, true);
+    else if (lower && !trans && !unit) GBLA_TRSV(true, false, false);
+    else if (lower && trans && unit) GBLA_TRSV(true, true, true);
+    else if (lower && trans && !unit) GBLA_TRSV(true, true, false);
+    else if (!lower && !trans && unit) GBLA_TRSV(false, false, true);
+    else if (!lower && !trans && !unit) GBLA_TRSV(false, false, false);
+    else if (!lower && trans && unit) GBLA_TRSV(false, true, true);
+    else GBLA_TRSV(false, true, false);
+#undef GBLA_TRSV
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template cudaError_t launch_trsv<double>(bool, bool, bool, int, int, const double*, int, double*,
+                                         int, unsigned*, int*, cudaStream_t);
+template cudaError_t launch_trsv<float>(bool, bool, bool, int, int, const float*, int, double*,
+                                        int, unsigned*, int*, cudaStream_t);
+
+}  // namespace gbla

@@ -1,0 +1,64 @@
+"""CPU-side checks of the C ABI: the library loads, exports every symbol the
+header declares, and rejects invalid arguments before touching the device."""
+import ctypes
+import os
+
+import pytest
+
+from paper_1511_07174_gb300 import _lib
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1511_07174_gb300 import build
+    build.build()
+    return _lib.load()
+
+
+def test_header_symbols_exported(lib):
+    syms = _lib.header_symbols()
+    assert len(syms) >= 10
+    for name in syms:
+        assert hasattr(lib, name), name
+    # every declared symbol has a ctypes signature in the binding
+    assert set(syms) <= set(_lib._SIGS), set(syms) - set(_lib._SIGS)
+
+
+def test_version_and_status(lib):
+    assert b"gbla" in lib.gbla_version()
+    assert _lib.status_string(0) == "success"
+    assert "workspace" in _lib.status_string(1001)
+    assert _lib.status_string(-3) == "invalid argument"
+
+
+def test_wait_timeout_roundtrip(lib):
+    old = lib.gbla_get_wait_timeout_ns()
+    lib.gbla_set_wait_timeout_ns(12345)
+    assert lib.gbla_get_wait_timeout_ns() == 12345
+    lib.gbla_set_wait_timeout_ns(old)
+
+
+def test_invalid_arguments_rejected_on_host(lib):
+    v = ctypes.c_void_p(0)
+    assert lib.gbla_lu_factor(-1, v, 1, v, v, 0, v, 0, v) == -1
+    assert lib.gbla_lu_factor(4, v, 4, v, v, 0, v, 0, v) == -2
+    fake = ctypes.c_void_p(256)
+    assert lib.gbla_lu_factor(4, fake, 3, fake, fake, 0, fake, 0, v) == -3
+    assert lib.gbla_lu_factor(4, fake, 4, fake, fake, 48, fake, 0, v) == -6
+    assert lib.gbla_lu_factor(4, fake, 4, fake, fake, 0, v, 0, v) == 1001
+    assert lib.gbla_lu_solve(2, 4, 1, fake, 4, fake, fake, 4, fake, fake, 1 << 20, v) == -1
+    assert lib.gbla_lu_solve(0, 4, -1, fake, 4, fake, fake, 4, fake, fake, 1 << 20, v) == -3
+    assert lib.gbla_lu_factor_mixed(4, fake, 4, fake, 4, fake, fake, 9, 0, fake, 1 << 20, v) == -8
+    assert lib.gbla_backward_error(4, 1, fake, 2, fake, 4, fake, 4, fake, fake, 1 << 20, v) == -4
+    opts = _lib.GmresirOpts(1e-14, 1e-8, 10, 500)
+    st = _lib.GmresirStats()
+    assert lib.gbla_gmresir_solve(4, fake, 4, fake, 4, fake, fake, fake, ctypes.byref(opts),
+                                  ctypes.byref(st), fake, 1 << 20, v) == -9
+
+
+def test_workspace_sizes(lib):
+    assert lib.gbla_lu_factor_workspace(1000, 0) > 0
+    assert lib.gbla_lu_factor_workspace(1000, 40) == 0          # invalid nb
+    assert lib.gbla_lu_factor_mixed_workspace(1000, 256, 3) > lib.gbla_lu_factor_workspace(1000, 256)
+    assert lib.gbla_gmresir_workspace(1000, 50) >= 1000 * 51 * 8
+    assert lib.gbla_lu_solve_workspace(100, 4) >= 100 * 4 * 8
