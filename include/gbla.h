@@ -54,12 +54,22 @@ typedef struct CUstream_st *gbla_stream_t; /* same type as cudaStream_t */
 #define GBLA_PREC_TF32 2 /* TF32 operands (nearest, ties away), FP32 accumulate, tensor cores */
 #define GBLA_PREC_BF16 3 /* BF16 operands with power-of-two row/column scaling, FP32 accumulate */
 #define GBLA_PREC_FP16 4 /* FP16 operands with power-of-two row/column scaling, FP32 accumulate */
+/* Split-operand variants: every scaled FP32 operand x is written as hi + lo
+ * with hi = rn16(x), lo = rn16(x - hi), and the update accumulates
+ * hi*hi + hi*lo + lo*hi in one FP32 tensor-memory accumulator (three times the
+ * tensor-core work, close to FP32 accuracy for FP16). */
+#define GBLA_PREC_FP16X3 5
+#define GBLA_PREC_BF16X3 6
 
 /* Library version string (static storage). */
 const char *gbla_version(void);
 
 /* Human-readable text for a return code (static storage). */
 const char *gbla_status_string(int status);
+
+/* Text of the last CUDA runtime failure seen by a gbla call on this host
+ * thread (CUDA error name, failing call, message); "" if none. */
+const char *gbla_last_error(void);
 
 /*
  * Limit, in nanoseconds, for every inter-CTA wait of later calls (panel
@@ -83,7 +93,7 @@ uint64_t gbla_get_wait_timeout_ns(void);
  *   lda    leading dimension (>= max(1, n))
  *   ipiv   n ints, output pivots (1-based)
  *   d_info one int, output (see conventions); set to 0 by the call
- *   nb     block size in [32, 512], multiple of 32; 0 = default (256)
+ *   nb     block size in [32, 256], multiple of 32; 0 = default (256)
  * ------------------------------------------------------------------------ */
 size_t gbla_lu_factor_workspace(int n, int nb);
 int gbla_lu_factor(int n, double *A, int lda, int *ipiv, int *d_info, int nb,
@@ -106,9 +116,9 @@ int gbla_lu_solve(int trans, int n, int nrhs, const double *LU, int lda, const i
  * set to fp32(A) and factored in place: panels in FP64 arithmetic rounded to
  * FP32, the U row block by FP32 substitution, the trailing update in the
  * precision `prec` (GBLA_PREC_*): tensor-core (tcgen05, TMEM accumulator,
- * TMA-fed) for TF32 / BF16 / FP16, FP32 SIMT for FP32. BF16 / FP16 operands
- * carry one power-of-two scale per row of L21 and per column of U12, undone
- * exactly in the epilogue. A (FP64) is only read.
+ * TMA-fed) for TF32 / BF16 / FP16 and the split variants, FP32 SIMT for FP32.
+ * 16-bit operands carry one power-of-two scale per row of L21 and per column
+ * of U12, undone exactly in the epilogue. A (FP64) is only read.
  * ------------------------------------------------------------------------ */
 size_t gbla_lu_factor_mixed_workspace(int n, int nb, int prec);
 int gbla_lu_factor_mixed(int n, const double *A, int lda, float *F, int ldf, int *ipiv,

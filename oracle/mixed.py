@@ -15,7 +15,10 @@ Per block column:
        bf16 / fp16 -- each row of L21 and each column of U12 multiplied by a
          power of two 2^e chosen so that its largest magnitude lies in
          [2^14, 2^15), then rounded to nearest-even in the 16-bit format; the
-         FP32 product is multiplied by 2^-(e_row + e_col), which is exact.
+         FP32 product is multiplied by 2^-(e_row + e_col), which is exact;
+       fp16x3 / bf16x3 -- the scaled operands split as hi + lo (hi rounded,
+         lo = rounded remainder) and the product taken as
+         hi*hi + hi*lo + lo*hi in one FP32 accumulation.
 A library matrix product (numpy float32 @) serves as step 3's product.
 """
 import numpy as np
@@ -76,6 +79,21 @@ def lowprec_product(L21, U12, prec):
         a = rnd(np.ldexp(L21, ea[:, None]))
         b = rnd(np.ldexp(U12, eb[None, :]))
         d = (a.astype(np.float32) @ b.astype(np.float32)).astype(np.float64)
+        return np.ldexp(d, -(ea[:, None] + eb[None, :]))
+    if prec in ("fp16x3", "bf16x3"):
+        rnd = round_bf16 if prec == "bf16x3" else round_fp16
+        ea = sliver_exponent(np.abs(L21).max(axis=1) if L21.shape[1] else np.zeros(L21.shape[0]))
+        eb = sliver_exponent(np.abs(U12).max(axis=0) if U12.shape[0] else np.zeros(U12.shape[1]))
+        a = to_fp32(np.ldexp(L21, ea[:, None]))
+        b = to_fp32(np.ldexp(U12, eb[None, :]))
+        ahi = rnd(a)
+        alo = rnd(a - ahi)
+        bhi = rnd(b)
+        blo = rnd(b - bhi)
+        # one FP32-accumulated product over the concatenated K: hi*hi + hi*lo + lo*hi
+        A3 = np.concatenate([ahi, ahi, alo], axis=1).astype(np.float32)
+        B3 = np.concatenate([bhi, blo, bhi], axis=0).astype(np.float32)
+        d = (A3 @ B3).astype(np.float64)
         return np.ldexp(d, -(ea[:, None] + eb[None, :]))
     raise ValueError(prec)
 

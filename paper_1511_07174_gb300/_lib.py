@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgbla.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "gbla.h")
 
-GBLA_PREC = {"fp32": 1, "tf32": 2, "bf16": 3, "fp16": 4}
+GBLA_PREC = {"fp32": 1, "tf32": 2, "bf16": 3, "fp16": 4, "fp16x3": 5, "bf16x3": 6}
 GBLA_INFO_TIMEOUT = -1000
 GBLA_ERR_NOT_CONVERGED = 1004
 
@@ -32,6 +32,7 @@ class GmresirStats(ctypes.Structure):
 _SIGS = {
     "gbla_version": ([], ctypes.c_char_p),
     "gbla_status_string": ([_i], ctypes.c_char_p),
+    "gbla_last_error": ([], ctypes.c_char_p),
     "gbla_set_wait_timeout_ns": ([ctypes.c_uint64], None),
     "gbla_get_wait_timeout_ns": ([], ctypes.c_uint64),
     "gbla_lu_factor_workspace": ([_i, _i], _sz),

@@ -17,7 +17,8 @@ PREC = _lib.GBLA_PREC
 class GblaError(RuntimeError):
     def __init__(self, name, rc):
         self.rc = rc
-        super().__init__("%s failed: %d (%s)" % (name, rc, _lib.status_string(rc)))
+        detail = _lib.load().gbla_last_error().decode() if rc == 1002 else ""
+        super().__init__("%s failed: %d (%s) %s" % (name, rc, _lib.status_string(rc), detail))
 
 
 def _check(name, rc):

@@ -6,6 +6,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
+#include <unordered_map>
 
 #include "internal.h"
 
@@ -35,12 +37,48 @@ const DeviceProps& device_props() {
   return p;
 }
 
-static int cuda_status(cudaError_t e) { return e == cudaSuccess ? GBLA_OK : GBLA_ERR_CUDA; }
+cudaError_t ensure_dyn_smem_ptr(const void* func, size_t bytes) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, size_t> granted;
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = granted.find(func);
+  if (it != granted.end() && bytes <= it->second) return cudaSuccess;
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, func);
+  if (e != cudaSuccess) return e;
+  const size_t optin = device_props().smem_optin;
+  const size_t cap = optin > fa.sharedSizeBytes ? optin - fa.sharedSizeBytes : 0;
+  if (bytes > cap) return cudaErrorInvalidValue;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
+  if (e == cudaSuccess) granted[func] = cap;
+  return e;
+}
 
-#define GBLA_TRY(expr)                       \
-  do {                                       \
-    cudaError_t _e = (expr);                 \
-    if (_e != cudaSuccess) return GBLA_ERR_CUDA; \
+static thread_local char g_last_error[256] = "";
+
+static void clear_error() { g_last_error[0] = 0; }
+
+static void record_error(cudaError_t e, const char* what, int line) {
+  snprintf(g_last_error, sizeof(g_last_error), "%s (%s) at api.cu:%d: %s", cudaGetErrorName(e), what,
+           line, cudaGetErrorString(e));
+}
+
+// the first failure of a call is kept; the outer wrappers do not overwrite it
+static int cuda_status_at(cudaError_t e, const char* what, int line) {
+  if (e == cudaSuccess) return GBLA_OK;
+  if (g_last_error[0] == 0) record_error(e, what, line);
+  return GBLA_ERR_CUDA;
+}
+#define cuda_status(e) cuda_status_at((e), #e, __LINE__)
+
+#define GBLA_TRY(expr)                                   \
+  do {                                                   \
+    cudaError_t _e = (expr);                             \
+    if (_e != cudaSuccess) {                             \
+      record_error(_e, #expr, __LINE__);                 \
+      return GBLA_ERR_CUDA;                              \
+    }                                                    \
   } while (0)
 
 static bool aligned256(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 255) == 0; }
@@ -75,9 +113,9 @@ static size_t lu_work_layout(Carver& c, int n, int nb, int prec, LuWork* w) {
     w->eA = w->eB = nullptr;
     w->ldk = 0;
   }
-  if (prec == GBLA_PREC_BF16 || prec == GBLA_PREC_FP16 || prec == GBLA_PREC_TF32) {
+  if (prec_is_tensor(prec)) {
     const int elem = prec == GBLA_PREC_TF32 ? 4 : 2;
-    const int ldk = ((nb + 63) / 64) * 64;
+    const int ldk = ((prec_kmult(prec) * nb + 63) / 64) * 64;
     void* Ak = c.take<char>((size_t)std::max(n, 1) * ldk * elem);
     void* Bk = c.take<char>((size_t)std::max(n, 1) * ldk * elem);
     int* eA = c.take<int>((size_t)std::max(n, 1));
@@ -104,38 +142,38 @@ static cudaError_t blocked_lu(int n, Ts* A, int lda, int* ipiv, int* info, int n
       const int jb = std::min(kPanelWidth, k0 + kb - j0);
       e = launch_panel<Ts>(A + j0 + (size_t)j0 * lda, lda, n - j0, jb, j0, ipiv + j0, info,
                            w.slots, w.counters + j0 / kPanelWidth, s);
-      if (e != cudaSuccess) return e;
+      if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
       e = launch_laswp<Ts>(A, lda, n, k0, j0, j0 + jb, k0 + kb, ipiv, j0, j0 + jb, s);
-      if (e != cudaSuccess) return e;
+      if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
       const int nrest = k0 + kb - j0 - jb;
       if (nrest > 0) {
         e = launch_trsm_lunit<Ts, Tc_trsm>(A + j0 + (size_t)j0 * lda, lda,
                                            A + j0 + (size_t)(j0 + jb) * lda, lda, jb, nrest, 0,
                                            nullptr, 0, nullptr, s);
-        if (e != cudaSuccess) return e;
+        if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
         e = launch_gemm_simt<Ts>(n - j0 - jb, nrest, jb, (Ts)-1, A + (j0 + jb) + (size_t)j0 * lda,
                                  lda, A + j0 + (size_t)(j0 + jb) * lda, lda, false, (Ts)1,
                                  A + (j0 + jb) + (size_t)(j0 + jb) * lda, lda, false, s);
-        if (e != cudaSuccess) return e;
+        if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
       }
     }
     e = launch_laswp<Ts>(A, lda, n, 0, k0, k0 + kb, n, ipiv, k0, k0 + kb, s);
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
     const int nt = n - k0 - kb;
     if (nt <= 0) continue;
-    const bool tensor = (prec == GBLA_PREC_BF16 || prec == GBLA_PREC_FP16 || prec == GBLA_PREC_TF32);
+    const bool tensor = prec_is_tensor(prec);
     e = launch_trsm_lunit<Ts, Tc_trsm>(A + k0 + (size_t)k0 * lda, lda, A + k0 + (size_t)(k0 + kb) * lda,
                                        lda, kb, nt, tensor ? prec : 0, w.Bk, w.ldk, w.eB, s);
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
     if (tensor) {
       if constexpr (sizeof(Ts) == 4) {
         e = launch_convert_rows(reinterpret_cast<const float*>(A + (k0 + kb) + (size_t)k0 * lda), lda,
                                 nt, kb, prec, w.Ak, w.ldk, w.eA, s);
-        if (e != cudaSuccess) return e;
-        e = launch_gemm_tc(prec, nt, nt, kb, w.Ak, w.ldk, w.Bk, w.ldk, w.eA, w.eB,
+        if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
+        e = launch_gemm_tc(prec_mma_kind(prec), nt, nt, prec_kmult(prec) * kb, w.Ak, w.ldk, w.Bk, w.ldk, w.eA, w.eB,
                            reinterpret_cast<float*>(A + (k0 + kb) + (size_t)(k0 + kb) * lda), lda,
                            info, s);
-        if (e != cudaSuccess) return e;
+        if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
       } else {
         return cudaErrorInvalidValue;
       }
@@ -143,7 +181,7 @@ static cudaError_t blocked_lu(int n, Ts* A, int lda, int* ipiv, int* info, int n
       e = launch_gemm_simt<Ts>(nt, nt, kb, (Ts)-1, A + (k0 + kb) + (size_t)k0 * lda, lda,
                                A + k0 + (size_t)(k0 + kb) * lda, lda, false, (Ts)1,
                                A + (k0 + kb) + (size_t)(k0 + kb) * lda, lda, false, s);
-      if (e != cudaSuccess) return e;
+      if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
     }
   }
   return cudaSuccess;
@@ -172,6 +210,8 @@ const char* gbla_status_string(int status) {
   }
 }
 
+const char* gbla_last_error(void) { return g_last_error; }
+
 void gbla_set_wait_timeout_ns(uint64_t ns) { g_wait_ns = ns; }
 uint64_t gbla_get_wait_timeout_ns(void) { return g_wait_ns; }
 
@@ -185,6 +225,7 @@ size_t gbla_lu_factor_workspace(int n, int nb) {
 
 int gbla_lu_factor(int n, double* A, int lda, int* ipiv, int* d_info, int nb, void* d_work,
                    size_t work_bytes, gbla_stream_t stream) {
+  clear_error();
   if (n < 0) return -1;
   if (n > 0 && !A) return -2;
   if (lda < std::max(1, n)) return -3;
@@ -210,13 +251,14 @@ int gbla_lu_factor(int n, double* A, int lda, int* ipiv, int* d_info, int nb, vo
 // ---------------------------------------------------------------------------
 size_t gbla_lu_factor_mixed_workspace(int n, int nb, int prec) {
   nb = check_nb(nb);
-  if (n < 0 || nb < 0 || prec < GBLA_PREC_FP32 || prec > GBLA_PREC_FP16) return 0;
+  if (n < 0 || nb < 0 || prec < GBLA_PREC_FP32 || prec > GBLA_PREC_BF16X3) return 0;
   Carver c(nullptr, 0);
   return lu_work_layout(c, n, nb, prec, nullptr);
 }
 
 int gbla_lu_factor_mixed(int n, const double* A, int lda, float* F, int ldf, int* ipiv, int* d_info,
                          int prec, int nb, void* d_work, size_t work_bytes, gbla_stream_t stream) {
+  clear_error();
   if (n < 0) return -1;
   if (n > 0 && !A) return -2;
   if (lda < std::max(1, n)) return -3;
@@ -224,7 +266,7 @@ int gbla_lu_factor_mixed(int n, const double* A, int lda, float* F, int ldf, int
   if (ldf < std::max(1, n)) return -5;
   if (n > 0 && !ipiv) return -6;
   if (!d_info) return -7;
-  if (prec < GBLA_PREC_FP32 || prec > GBLA_PREC_FP16) return -8;
+  if (prec < GBLA_PREC_FP32 || prec > GBLA_PREC_BF16X3) return -8;
   nb = check_nb(nb);
   if (nb < 0) return -9;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -255,6 +297,7 @@ size_t gbla_lu_solve_workspace(int n, int nrhs) {
 
 int gbla_lu_solve(int trans, int n, int nrhs, const double* LU, int lda, const int* ipiv, double* B,
                   int ldb, int* d_info, void* d_work, size_t work_bytes, gbla_stream_t stream) {
+  clear_error();
   if (trans != 0 && trans != 1) return -1;
   if (n < 0) return -2;
   if (nrhs < 0) return -3;
@@ -304,6 +347,7 @@ size_t gbla_backward_error_workspace(int n, int nrhs) {
 int gbla_backward_error(int n, int nrhs, const double* A, int lda, const double* X, int ldx,
                         const double* B, int ldb, double* d_beta, void* d_work, size_t work_bytes,
                         gbla_stream_t stream) {
+  clear_error();
   if (n < 0) return -1;
   if (nrhs < 0) return -2;
   if (n > 0 && !A) return -3;
@@ -404,6 +448,7 @@ int gbla_gmresir_solve(int n, const double* A, int lda, const float* F, int ldf,
                        const double* b, double* x, const gbla_gmresir_opts* opts,
                        gbla_gmresir_stats* stats, void* d_work, size_t work_bytes,
                        gbla_stream_t stream) {
+  clear_error();
   if (n < 0) return -1;
   if (n > 0 && !A) return -2;
   if (lda < std::max(1, n)) return -3;

@@ -67,14 +67,33 @@ GBLA_DEVINL uint32_t f32_to_tf32_rna(float x) {
   return r;
 }
 
-template <int KIND>
-GBLA_DEVINL void store_lowp(void* base, size_t idx, float v) {
+// Store one scaled operand value into a K-major row `row` (K elements per
+// segment). Plain kinds: row[k] = round(v). Split kinds (hi = round(v),
+// lo = round(v - hi), v - hi exact in FP32): the L21 pattern (LEFT) is
+// [hi | hi | lo], the U12 pattern is [hi | lo | hi], so that the three
+// segment products sum to hi*hi + hi*lo + lo*hi.
+template <int KIND, bool LEFT>
+GBLA_DEVINL void store_lowp(void* base, size_t row, int K, int k, float v) {
   if constexpr (KIND == GBLA_PREC_BF16) {
-    reinterpret_cast<__nv_bfloat16*>(base)[idx] = __float2bfloat16_rn(v);
+    reinterpret_cast<__nv_bfloat16*>(base)[row + k] = __float2bfloat16_rn(v);
   } else if constexpr (KIND == GBLA_PREC_FP16) {
-    reinterpret_cast<__half*>(base)[idx] = __float2half_rn(v);
+    reinterpret_cast<__half*>(base)[row + k] = __float2half_rn(v);
+  } else if constexpr (KIND == GBLA_PREC_TF32) {
+    reinterpret_cast<uint32_t*>(base)[row + k] = f32_to_tf32_rna(v);
+  } else if constexpr (KIND == GBLA_PREC_FP16X3) {
+    __half* b = reinterpret_cast<__half*>(base) + row;
+    const __half hi = __float2half_rn(v);
+    const __half lo = __float2half_rn(v - __half2float(hi));
+    b[k] = hi;
+    b[K + k] = LEFT ? hi : lo;
+    b[2 * K + k] = LEFT ? lo : hi;
   } else {
-    reinterpret_cast<uint32_t*>(base)[idx] = f32_to_tf32_rna(v);
+    __nv_bfloat16* b = reinterpret_cast<__nv_bfloat16*>(base) + row;
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+    b[k] = hi;
+    b[K + k] = LEFT ? hi : lo;
+    b[2 * K + k] = LEFT ? lo : hi;
   }
 }
 
@@ -156,7 +175,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const int r = lane + 32 * q;
-          if (r < w) store_lowp<OUT>(outK, (size_t)col * ldk + r, ldexpf((float)(Ts)x[q][c], e));
+          if (r < w) store_lowp<OUT, false>(outK, (size_t)col * ldk, w, r, ldexpf((float)(Ts)x[q][c], e));
         }
       }
     }
@@ -170,24 +189,21 @@ cudaError_t launch_trsm_lunit(const Ts* L, int ldl, Ts* B, int ldb, int w, int N
   if (w > 256) return cudaErrorInvalidValue;
   const size_t smem = (size_t)32 * w * sizeof(Tc);
   const dim3 grid((N + kTrsmCols - 1) / kTrsmCols);
-  static bool attr[4] = {false, false, false, false};
-#define GBLA_TRSM_CASE(K, IDX)                                                                   \
-  {                                                                                            \
-    auto kfn = trsm_lunit_kernel<Ts, Tc, K>;                                                   \
-    if (!attr[IDX]) {                                                                          \
-      cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
-                                           (int)(64 * 1024 + 32 * 256 * 8));                   \
-      if (e != cudaSuccess) return e;                                                          \
-      attr[IDX] = true;                                                                        \
-    }                                                                                          \
-    kfn<<<grid, 256, smem, s>>>(L, ldl, B, ldb, w, N, outK, ldk, outE);                        \
-    break;                                                                                     \
+#define GBLA_TRSM_CASE(K, IDX)                                                       \
+  {                                                                                \
+    auto kfn = trsm_lunit_kernel<Ts, Tc, K>;                                       \
+    cudaError_t ea = ensure_dyn_smem(kfn, smem);                                   \
+    if (ea != cudaSuccess) return ea;                                              \
+    kfn<<<grid, 256, smem, s>>>(L, ldl, B, ldb, w, N, outK, ldk, outE);            \
+    break;                                                                         \
   }
   switch (out_kind) {
     case 0: GBLA_TRSM_CASE(0, 0)
     case GBLA_PREC_BF16: GBLA_TRSM_CASE(GBLA_PREC_BF16, 1)
     case GBLA_PREC_FP16: GBLA_TRSM_CASE(GBLA_PREC_FP16, 2)
     case GBLA_PREC_TF32: GBLA_TRSM_CASE(GBLA_PREC_TF32, 3)
+    case GBLA_PREC_FP16X3: GBLA_TRSM_CASE(GBLA_PREC_FP16X3, 4)
+    case GBLA_PREC_BF16X3: GBLA_TRSM_CASE(GBLA_PREC_BF16X3, 5)
     default: return cudaErrorInvalidValue;
   }
 #undef GBLA_TRSM_CASE
@@ -353,7 +369,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int t = 0; t < 2; ++t) {
           const int kk = lane * 2 + t, k = k0 + kk;
-          if (k < K) store_lowp<KIND>(outK, (size_t)mr * ldk + k, ldexpf(tile[kk][mm], es[mm]));
+          if (k < K) store_lowp<KIND, true>(outK, (size_t)mr * ldk, K, k, ldexpf(tile[kk][mm], es[mm]));
         }
       }
     }
@@ -374,6 +390,12 @@ cudaError_t launch_convert_rows(const float* F, int ldf, int M, int K, int kind,
       break;
     case GBLA_PREC_TF32:
       convert_rows_kernel<GBLA_PREC_TF32><<<grid, 256, 0, s>>>(F, ldf, M, K, outK, ldk, outE);
+      break;
+    case GBLA_PREC_FP16X3:
+      convert_rows_kernel<GBLA_PREC_FP16X3><<<grid, 256, 0, s>>>(F, ldf, M, K, outK, ldk, outE);
+      break;
+    case GBLA_PREC_BF16X3:
+      convert_rows_kernel<GBLA_PREC_BF16X3><<<grid, 256, 0, s>>>(F, ldf, M, K, outK, ldk, outE);
       break;
     default:
       return cudaErrorInvalidValue;
@@ -430,14 +452,10 @@ cudaError_t launch_ipiv_to_perm(int n, const int* ipiv, int* perm, cudaStream_t 
   if (n <= 0) return cudaSuccess;
   const DeviceProps& dp = device_props();
   const size_t bytes = (size_t)n * sizeof(int);
-  const int use_smem = bytes <= dp.smem_optin ? 1 : 0;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(ipiv_to_perm_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)dp.smem_optin);
-    if (e != cudaSuccess) return e;
-    attr = true;
+  const int use_smem = bytes + 1024 <= dp.smem_optin ? 1 : 0;
+  if (use_smem) {
+    cudaError_t ea = ensure_dyn_smem(ipiv_to_perm_kernel, bytes);
+    if (ea != cudaSuccess) return ea;
   }
   ipiv_to_perm_kernel<<<1, 1024, use_smem ? bytes : 0, s>>>(n, ipiv, perm, use_smem);
   return cudaGetLastError();

@@ -313,19 +313,13 @@ cudaError_t launch_gemm_tc(int kind, int M, int N, int K, const void* Ak, int ld
   if (!encode_kmajor(&tb, kind, Bk, K, N, ldbk)) return cudaErrorInvalidValue;
   TcArgs a{M, N, K, C, ldc, eA, eB, info, wait_timeout_ns()};
   const dim3 grid((M + kTcBM - 1) / kTcBM, (N + kTcBN - 1) / kTcBN);
-  static bool attr[5] = {false, false, false, false, false};
   switch (kind) {
-#define GBLA_TC_CASE(K)                                                                         \
-  case K: {                                                                                   \
-    if (!attr[K]) {                                                                           \
-      cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<K>,                                 \
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,       \
-                                           kTcSmemBytes);                                     \
-      if (e != cudaSuccess) return e;                                                         \
-      attr[K] = true;                                                                         \
-    }                                                                                         \
-    gemm_tc_kernel<K><<<grid, 128, kTcSmemBytes, s>>>(ta, tb, a);                              \
-    break;                                                                                    \
+#define GBLA_TC_CASE(K)                                                        \
+  case K: {                                                                  \
+    cudaError_t ea = ensure_dyn_smem(gemm_tc_kernel<K>, (size_t)kTcSmemBytes); \
+    if (ea != cudaSuccess) return ea;                                        \
+    gemm_tc_kernel<K><<<grid, 128, kTcSmemBytes, s>>>(ta, tb, a);             \
+    break;                                                                   \
   }
     GBLA_TC_CASE(GBLA_PREC_TF32)
     GBLA_TC_CASE(GBLA_PREC_BF16)

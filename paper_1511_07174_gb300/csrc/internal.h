@@ -19,6 +19,15 @@ struct DeviceProps {
 };
 const DeviceProps& device_props();
 
+// Raise a kernel's dynamic shared-memory limit to at least `bytes` (tracked
+// per kernel; the limit must leave room for the kernel's static shared
+// memory). Returns cudaErrorInvalidValue when the request cannot fit.
+cudaError_t ensure_dyn_smem_ptr(const void* func, size_t bytes);
+template <typename F>
+cudaError_t ensure_dyn_smem(F* func, size_t bytes) {
+  return ensure_dyn_smem_ptr(reinterpret_cast<const void*>(func), bytes);
+}
+
 // ---- workspace carving -----------------------------------------------------
 struct Carver {
   char* base;
@@ -42,6 +51,16 @@ struct Carver {
     return p;
   }
 };
+
+// ---- precision kinds of the mixed trailing update ---------------------------
+inline bool prec_is_tensor(int p) { return p >= GBLA_PREC_TF32 && p <= GBLA_PREC_BF16X3; }
+inline bool prec_is_split(int p) { return p == GBLA_PREC_FP16X3 || p == GBLA_PREC_BF16X3; }
+// tcgen05 operand kind executing the update
+inline int prec_mma_kind(int p) {
+  return p == GBLA_PREC_FP16X3 ? GBLA_PREC_FP16 : (p == GBLA_PREC_BF16X3 ? GBLA_PREC_BF16 : p);
+}
+// K-major copies hold kmult * K elements per row ([hi|hi|lo] for L21, [hi|lo|hi] for U12)
+inline int prec_kmult(int p) { return prec_is_split(p) ? 3 : 1; }
 
 // ---- kernel launchers (all stream-ordered; return cudaError_t) -------------
 constexpr int kPanelWidth = 32;  // inner panel width handled by the cooperative kernel

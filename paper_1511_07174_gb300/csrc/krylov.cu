@@ -277,13 +277,8 @@ cudaError_t launch_mgs_step(int n, int j, double* V, int ldv, const double* w, d
   const int S = (n + C - 1) / C;
   const size_t smem = (size_t)S * sizeof(double);
   if (smem > dp.smem_optin) return cudaErrorInvalidValue;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(mgs_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)dp.smem_optin);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  cudaError_t ea = ensure_dyn_smem(mgs_step_kernel, smem);
+  if (ea != cudaSuccess) return ea;
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   GmresState* stp = static_cast<GmresState*>(st);

@@ -198,14 +198,8 @@ cudaError_t launch_panel(Ts* A, int lda, int m, int w, int row0, int* ipiv, int*
   C = (m + R - 1) / R;
   size_t smem = ((size_t)w * R + 2 * kPanelWidth) * sizeof(double);
   if (smem > dp.smem_optin) return cudaErrorInvalidValue;
-  static bool attr_done[2] = {false, false};
-  const int which = sizeof(Ts) == 8 ? 0 : 1;
-  if (!attr_done[which]) {
-    cudaError_t e = cudaFuncSetAttribute(panel_kernel<Ts>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)dp.smem_optin);
-    if (e != cudaSuccess) return e;
-    attr_done[which] = true;
-  }
+  cudaError_t ea = ensure_dyn_smem(panel_kernel<Ts>, smem);
+  if (ea != cudaSuccess) return ea;
   uint64_t wait_ns = wait_timeout_ns();
   void* args[] = {&A, &lda, &m, &w, &row0, &R, &ipiv, &info, &slots, &counter, &wait_ns};
   return cudaLaunchCooperativeKernel((const void*)panel_kernel<Ts>, dim3(C), dim3(kPanelThreads),

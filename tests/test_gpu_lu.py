@@ -116,7 +116,8 @@ def test_backward_error_kernel_matches_oracle():
     B = A @ X + 1e-9 * inputs.normal((n, nrhs), seed=5)
     beta = api.backward_error(A.to(DEV), X.to(DEV), B.to(DEV)).cpu().numpy()
     beta_o = oracle.backward_error(np.asfortranarray(A.numpy()), X.numpy(), B.numpy())
-    assert np.allclose(beta, beta_o, rtol=1e-10, atol=0)
+    # both sides round r = b - A x differently; |d beta| <= 2 gamma_n (Higham 3.5)
+    assert np.abs(beta - beta_o).max() <= 2 * n * 2.0 ** -53
 
 
 def test_wait_timeout_reports_status():

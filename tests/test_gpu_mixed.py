@@ -25,8 +25,16 @@ from paper_1511_07174_gb300 import api, inputs
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
-UNIT = {"fp32": 2.0 ** -24, "tf32": 2.0 ** -11, "bf16": 2.0 ** -8, "fp16": 2.0 ** -11}
-PRECS = ["fp32", "tf32", "bf16", "fp16"]
+UNIT = {"fp32": 2.0 ** -24, "tf32": 2.0 ** -11, "bf16": 2.0 ** -8, "fp16": 2.0 ** -11,
+        "fp16x3": 2.0 ** -21, "bf16x3": 2.0 ** -16}
+PRECS = ["fp32", "tf32", "bf16", "fp16", "fp16x3", "bf16x3"]
+
+
+def _expected_to_converge(prec, kappa):
+    """GMRES-IR with restarted GMRES(50) is expected to reach 1e-14 when the
+    preconditioned matrix M^{-1} A = I + E has ||E|| ~ kappa u_p of order one or
+    less; the test asks for it where kappa * u_p <= 10."""
+    return kappa * UNIT[prec] <= 10.0
 
 
 def _mixed(A, prec, nb):
@@ -69,6 +77,8 @@ def test_mixed_factor_bound_and_oracle(prec, n, nb):
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("kappa", [1e2, 1e4, 1e6])
 def test_gmresir_small(prec, kappa):
+    if not _expected_to_converge(prec, kappa):
+        pytest.skip("kappa * u_p > 10: outside the refinement's convergence range")
     n = 600
     UV = (inputs.haar(n, 4), inputs.haar(n, 5))
     A = inputs.haar_kappa(n, kappa, UV=UV)

@@ -95,7 +95,7 @@ def test_sliver_exponent_range():
     assert M.sliver_exponent(np.array([1e-35]))[0] == M.SCALE_CLAMP     # clamped
 
 
-@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16", "fp16"])
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16", "fp16", "fp16x3", "bf16x3"])
 @pytest.mark.parametrize("n,nb", [(1, 4), (37, 8), (96, 32)])
 def test_lowprec_lu_dyadic_exact(prec, n, nb):
     A, L0, U0, perm = inputs.dyadic_lu(n, seed=500 + n)
@@ -116,7 +116,7 @@ def test_lowprec_lu_fp32_close_to_fp64():
 
 
 @pytest.mark.parametrize("prec,kappa,max_outer", [("fp32", 1e2, 3), ("bf16", 1e4, 10),
-                                                   ("fp16", 1e4, 10)])
+                                                   ("fp16", 1e4, 10), ("fp16x3", 1e6, 4)])
 def test_gmres_ir_oracle_converges(prec, kappa, max_outer):
     n = 160
     A = inputs.haar_kappa(n, kappa, seed_u=4, seed_v=5).numpy()
@@ -128,3 +128,17 @@ def test_gmres_ir_oracle_converges(prec, kappa, max_outer):
     assert st["converged"], st
     assert oracle.backward_error(A, x, b)[0] <= 1e-14
     assert np.abs(x - x_true).max() <= 1e-14 * kappa * 100 * np.abs(x_true).max()
+
+
+def test_split_product_accuracy():
+    """hi*hi + hi*lo + lo*hi recovers the FP32 product to ~2^-21 (fp16x3) and
+    ~2^-16 (bf16x3) relative, far better than one 16-bit pass."""
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((64, 48))
+    B = rng.standard_normal((48, 40))
+    exact = A @ B
+    scale = np.abs(A).dot(np.abs(B)).max()
+    err = {p: np.abs(M.lowprec_product(A, B, p) - exact).max() / scale
+           for p in ("fp16", "fp16x3", "bf16", "bf16x3", "fp32")}
+    assert err["fp16x3"] <= 2.0 ** -20 and err["fp16x3"] < err["fp16"] / 50
+    assert err["bf16x3"] <= 2.0 ** -15 and err["bf16x3"] < err["bf16"] / 50
