@@ -1,0 +1,441 @@
+"""Benchmark: dense LU solve at n = 16384, mixed precision + GMRES-IR vs FP64.
+
+Workload (synthetic): three n x n systems A x = b with A = U diag(s) V^t, U, V
+Haar orthogonal (QR of Gaussian, seeds 4 and 5), s geometric from 1 to
+1/kappa for kappa in {1e2, 1e4, 1e6}, x_true ~ N(0, 1) (seed 6), b = A x_true.
+One step = solve all three to normwise backward error <= 1e-14: low-precision
+LU (FP32 working matrix, tensor-core trailing update) + GMRES-based iterative
+refinement in FP64. Metric: TFLOP/s counted as 2/3 n^3 per solve.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0). Inputs (2 GiB FP64 per matrix) are larger than
+the 129 MB L2, so no flush is needed between steps. Under torchrun every rank
+runs its own replica of the workload (the solver does not shard: replicas only)
+and the value is the work of all ranks over the slowest rank's time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+METRIC = "LU solve TFLOP/s (2/3n^3) n=16384: mixed+GMRES-IR vs FP64 at 1e-14 bkwd err"
+KAPPAS = (1e2, 1e4, 1e6)
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (DFMA) nominal; the FP64 GEMM is measured against it
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=16384)
+    ap.add_argument("--prec", default="fp16x3")
+    ap.add_argument("--nb", type=int, default=256)
+    ap.add_argument("--restart", type=int, default=50)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--cpu-ksteps", type=int, default=8,
+                    help="elimination steps of the oracle sample (bounded CPU baseline)")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- distributed
+def dist_init(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return ws, rank
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------- helpers
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return dict(FALLBACK_PEAKS), "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while active."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload(n, device):
+    from paper_1511_07174_gb300 import inputs
+    U = inputs.haar(n, 4, device)
+    V = inputs.haar(n, 5, device)
+    x_true = inputs.normal((n,), 6, device)
+    As, bs = [], []
+    for kappa in KAPPAS:
+        A = inputs.haar_kappa(n, kappa, UV=(U, V), device=device)
+        As.append(A)
+        bs.append(A @ x_true)
+    del U, V
+    torch.cuda.synchronize() if device != "cpu" else None
+    return As, bs, x_true
+
+
+def lu_flops(n):
+    return 2.0 / 3.0 * float(n) ** 3
+
+
+def gemm_tc_algorithmic_flops(n, nb):
+    """2 * M * N * K summed over the trailing updates of the blocked LU."""
+    tot = 0.0
+    for k0 in range(0, n, nb):
+        kb = min(nb, n - k0)
+        nt = n - k0 - kb
+        if nt > 0:
+            tot += 2.0 * nt * nt * kb
+    return tot
+
+
+def panel_algorithmic_bytes(n, elem):
+    """Each inner panel (32 columns, rows k..n) is read once and written once."""
+    tot = 0.0
+    for j0 in range(0, n, 32):
+        tot += 2.0 * (n - j0) * min(32, n - j0) * elem
+    return tot
+
+
+def trsv_algorithmic_bytes(n, elem):
+    """One triangular solve reads its triangle once (n(n+1)/2 elements) plus the vector."""
+    return n * (n + 1) / 2.0 * elem + 2.0 * n * 8
+
+
+def oracle_sample(A_host, ksteps):
+    """Time the CPU oracle on the first `ksteps` elimination steps of the n x n matrix."""
+    import oracle
+    n = A_host.shape[0]
+    t0 = time.perf_counter()
+    oracle.getrf(A_host, ksteps=ksteps)
+    dt = time.perf_counter() - t0
+    flops = 0.0
+    for j in range(ksteps):
+        m = n - j - 1
+        flops += m + 2.0 * m * m
+    return flops, dt
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    n = args.n
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    As, bs, _ = make_workload(n, dev)
+    A_host = np.asfortranarray(As[1].cpu().numpy())
+    del As, bs
+    for _ in range(args.warmup):
+        oracle_sample(A_host, args.cpu_ksteps)
+    times, flops = [], 0.0
+    for _ in range(args.steps):
+        f, dt = oracle_sample(A_host, args.cpu_ksteps)
+        times.append(dt)
+        flops = f
+    tmean = sum(times) / len(times)
+    value = flops / tmean / 1e12
+    sample = ("first %d elimination steps of LU with partial pivoting on the n=%d, kappa=1e4 "
+              "matrix (%.3g flop), plain FP64 C oracle, 1 thread" % (args.cpu_ksteps, n, flops))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": tmean * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "n=%d dense LU with partial pivoting (oracle sample)" % n, "n": n},
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------- our arm
+def solve_all(api, As, bs, args, F):
+    stats = []
+    for A, b in zip(As, bs):
+        Fk, ipiv, info = api.lu_factor_mixed(A, prec=args.prec, nb=args.nb, F=F)
+        x, st = api.gmresir(A, Fk, ipiv, b, tol=1e-14, inner_tol=1e-8, max_outer=20,
+                            restart_m=args.restart)
+        st["x"] = x
+        stats.append(st)
+    return stats
+
+
+def run_ours(args, ws, rank):
+    from paper_1511_07174_gb300 import api
+    import __graft_entry__
+    __graft_entry__.build()
+    n = args.n
+    dev = "cuda"
+    As, bs, x_true = make_workload(n, dev)
+    F = torch.empty_strided((n, n), (1, n), dtype=torch.float32, device=dev)
+    nsys = len(As)
+
+    # warm-up; the first warm-up step records every kernel group to find the dominant one
+    api.prof_enable(api.KERNEL_KINDS)
+    api.prof_reset()
+    for w in range(max(args.warmup, 1)):
+        solve_all(api, As, bs, args, F)
+        if w == 0:
+            torch.cuda.synchronize()
+            per_kind = {k: api.prof_read(k) for k in api.KERNEL_KINDS}
+            api.prof_reset()
+            api.prof_enable([])
+    dominant = max(per_kind, key=lambda k: per_kind[k][1])
+
+    # timed region
+    api.prof_enable([dominant])
+    api.prof_reset()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    launches0 = api.launch_count()
+    barrier(ws)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    all_stats = []
+    for _ in range(args.steps):
+        all_stats.append(solve_all(api, As, bs, args, F))
+    ev1.record()
+    torch.cuda.synchronize()
+    barrier(ws)
+    launches = api.launch_count() - launches0
+    clk = clocks.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    ms_total = max_over_ranks(ms_total, ws)
+    ms_step = ms_total / args.steps
+    dom_count, dom_ms = api.prof_read(dominant)
+    api.prof_enable([])
+    value = ws * nsys * lu_flops(n) / (ms_step * 1e-3) / 1e12
+
+    # correctness of the last step: device backward error and independent CPU oracle matvec
+    import oracle
+    last = all_stats[-1]
+    betas_dev = [st["beta"] for st in last]
+    betas_oracle = []
+    if rank == 0:
+        for A, b, st in zip(As, bs, last):
+            betas_oracle.append(float(oracle.backward_error(
+                np.asfortranarray(A.cpu().numpy()), st["x"].cpu().numpy(), b.cpu().numpy())[0]))
+
+    # FP64 path at kappa = 1e4 (one timed solve after a small warm-up)
+    api.lu_factor(As[1][:1024, :1024].contiguous())
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    LU, ipiv, info = api.lu_factor(As[1])
+    x64 = api.lu_solve(LU, ipiv, bs[1])
+    e1.record()
+    torch.cuda.synchronize()
+    fp64_ms = e0.elapsed_time(e1)
+    fp64_beta = float(api.backward_error(As[1], x64, bs[1]).item())
+    del LU, x64
+
+    # end to end through the public API from pinned host buffers
+    hostA = [A.cpu().pin_memory() for A in As]
+    hostb = [b.cpu().pin_memory() for b in bs]
+    dA = [torch.empty_like(A) for A in As]
+    db = [torch.empty_like(b) for b in bs]
+    hx = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in As]
+    del As, bs
+    torch.cuda.synchronize()
+    barrier(ws)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(args.e2e_steps):
+        for k in range(nsys):
+            dA[k].copy_(hostA[k], non_blocking=True)
+            db[k].copy_(hostb[k], non_blocking=True)
+            Fk, ipiv, info = api.lu_factor_mixed(dA[k], prec=args.prec, nb=args.nb, F=F)
+            x, st = api.gmresir(dA[k], Fk, ipiv, db[k], tol=1e-14, max_outer=20,
+                                restart_m=args.restart)
+            hx[k].copy_(x, non_blocking=True)
+    t1.record()
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(t0.elapsed_time(t1) / args.e2e_steps, ws)
+    e2e_value = ws * nsys * lu_flops(n) / (e2e_ms * 1e-3) / 1e12
+    h2d = sum(int(h.numel() * h.element_size()) for h in hostA + hostb)
+    d2h = sum(int(h.numel() * h.element_size()) for h in hx)
+
+    # roofline of the dominant kernel group
+    pk, src = peaks()
+    steps_seen = args.steps
+    if dominant == "gemm_tc":
+        alg = gemm_tc_algorithmic_flops(n, args.nb) * nsys * steps_seen
+        achieved = alg / (dom_ms * 1e-3) / 1e12
+        peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+        bound, unit = "tensor", "TFLOP/s"
+        per_launch_units = "2*M*N*K of each rank-%d update (the split variant executes 3x on the tensor pipe)" % args.nb
+    elif dominant == "gemm_simt" and args.prec == "fp32":
+        alg = gemm_tc_algorithmic_flops(n, args.nb) * nsys * steps_seen
+        achieved = alg / (dom_ms * 1e-3) / 1e12
+        peak, bound, unit = None, "alu", "TFLOP/s"
+        per_launch_units = "2*M*N*K"
+    elif dominant == "panel":
+        alg = panel_algorithmic_bytes(n, 4) * nsys * steps_seen
+        achieved = alg / (dom_ms * 1e-3) / 1e9
+        peak, bound, unit = pk.get("hbm_gbs"), "hbm", "GB/s"
+        per_launch_units = "panel slab read + written once (32 columns x rows, FP32)"
+    elif dominant == "trsv":
+        alg = trsv_algorithmic_bytes(n, 4) * dom_count
+        achieved = alg / (dom_ms * 1e-3) / 1e9
+        peak, bound, unit = pk.get("hbm_gbs"), "hbm", "GB/s"
+        per_launch_units = "triangle of the FP32 factor read once + vector"
+    else:
+        alg = None
+        achieved, peak, bound, unit = None, pk.get("hbm_gbs"), "hbm", "GB/s"
+        per_launch_units = ""
+    roof = {"kernel": dominant, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": (achieved / peak) if (achieved and peak) else None, "traffic": None,
+            "peak_source": src, "launch_groups": dom_count, "ms_in_timed_region": dom_ms,
+            "algorithmic_units": per_launch_units}
+    prof_path = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof_path):
+        with open(prof_path) as f:
+            tr = json.load(f)
+        roof["traffic"] = tr.get(dominant)
+
+    # bounded CPU baseline: the oracle on the first k elimination steps of one system
+    cpu = None
+    if rank == 0:
+        Ah = np.asfortranarray(hostA[1].numpy())
+        flops, dt = oracle_sample(Ah, args.cpu_ksteps)
+        cpu = {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+               "sample": "first %d elimination steps of GEPP on the n=%d kappa=1e4 matrix "
+                         "(%.3g flop in %.1f s), plain FP64 C, 1 thread" % (args.cpu_ksteps, n, flops, dt)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "%s update, f32 factors, f64 refinement" % args.prec, "data": "synthetic",
+            "config": {"workload": "dense LU solve n=%d, 3 systems (kappa 1e2, 1e4, 1e6; Haar U,V; "
+                                   "geometric singular values), 1 RHS each, to backward error 1e-14"
+                                   % n,
+                       "n": n, "prec": args.prec, "nb": args.nb, "restart": args.restart,
+                       "systems_per_step": nsys, "parallelism": "replicas" if ws > 1 else "single",
+                       "l2": "no flush: each FP64 matrix (%.1f GiB) exceeds L2" % (n * n * 8 / 2 ** 30)},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "fp64_path": {"ms": fp64_ms, "tflops": lu_flops(n) / (fp64_ms * 1e-3) / 1e12,
+                          "beta": fp64_beta, "kappa": 1e4,
+                          "speedup_mixed_vs_fp64": fp64_ms / (ms_step / nsys)},
+            "refinement": [{"kappa": k, "outer": st["outer"], "inner": st["inner"],
+                            "beta_device": st["beta"], "beta_oracle": bo}
+                           for k, st, bo in zip(KAPPAS, last, betas_oracle)],
+            "kernel_ms_first_warmup_step": {k: round(v[1], 3) for k, v in per_kind.items() if v[0]},
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -72,6 +72,22 @@ const char *gbla_status_string(int status);
 const char *gbla_last_error(void);
 
 /*
+ * Instrumentation (off by default; nothing here changes results).
+ * gbla_launch_count: kernels this library has launched in this process.
+ * gbla_prof_enable(mask): bracket every later launch group of the kinds set
+ *   in mask (bit k = kind k) with a pair of CUDA events on its stream.
+ *   Kinds: 0 panel, 1 laswp, 2 trsm, 3 gemm_simt, 4 gemm_tc, 5 convert,
+ *   6 trsv, 7 matvec, 8 mgs, 9 gmres_update, 10 permute, 11 copy.
+ * gbla_prof_read: number of recorded groups of `kind` and their summed
+ *   device time in ms (waits for the events). gbla_prof_reset forgets them.
+ */
+uint64_t gbla_launch_count(void);
+const char *gbla_kernel_kind_name(int kind);
+void gbla_prof_enable(unsigned mask);
+void gbla_prof_reset(void);
+int gbla_prof_read(int kind, int *count, double *total_ms);
+
+/*
  * Limit, in nanoseconds, for every inter-CTA wait of later calls (panel
  * barrier, substitution chain). A wait that runs out writes GBLA_INFO_TIMEOUT
  * to d_info and the kernel returns. Default 2e9 (2 s). Process-wide; not

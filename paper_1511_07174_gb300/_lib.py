@@ -13,6 +13,8 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "gbla.h")
 
 GBLA_PREC = {"fp32": 1, "tf32": 2, "bf16": 3, "fp16": 4, "fp16x3": 5, "bf16x3": 6}
 GBLA_INFO_TIMEOUT = -1000
+KERNEL_KINDS = ["panel", "laswp", "trsm", "gemm_simt", "gemm_tc", "convert", "trsv", "matvec", "mgs",
+                "gmres_update", "permute", "copy"]
 GBLA_ERR_NOT_CONVERGED = 1004
 
 _vp = ctypes.c_void_p
@@ -34,6 +36,11 @@ _SIGS = {
     "gbla_status_string": ([_i], ctypes.c_char_p),
     "gbla_last_error": ([], ctypes.c_char_p),
     "gbla_set_wait_timeout_ns": ([ctypes.c_uint64], None),
+    "gbla_launch_count": ([], ctypes.c_uint64),
+    "gbla_kernel_kind_name": ([_i], ctypes.c_char_p),
+    "gbla_prof_enable": ([ctypes.c_uint], None),
+    "gbla_prof_reset": ([], None),
+    "gbla_prof_read": ([_i, ctypes.POINTER(_i), ctypes.POINTER(_d)], _i),
     "gbla_get_wait_timeout_ns": ([], ctypes.c_uint64),
     "gbla_lu_factor_workspace": ([_i, _i], _sz),
     "gbla_lu_factor": ([_i, _vp, _i, _vp, _vp, _i, _vp, _sz, _vp], _i),

@@ -168,3 +168,33 @@ def backward_error(A, X, B):
            L.gbla_backward_error(n, nrhs, _p(Ac), _ld(Ac), _p(Xc), _ld(Xc), _p(Bc), _ld(Bc), _p(beta),
                                  _p(ws), ws.numel(), _stream()))
     return beta[:nrhs]
+
+
+# ------------------------------------------------------------- instrumentation
+KERNEL_KINDS = _lib.KERNEL_KINDS
+
+
+def launch_count():
+    """Kernels libgbla has launched in this process."""
+    return int(_lib.load().gbla_launch_count())
+
+
+def prof_enable(kinds):
+    """Bracket later launch groups of the given kinds (names) with CUDA events."""
+    mask = 0
+    for k in kinds:
+        mask |= 1 << KERNEL_KINDS.index(k)
+    _lib.load().gbla_prof_enable(mask)
+
+
+def prof_reset():
+    _lib.load().gbla_prof_reset()
+
+
+def prof_read(kind):
+    """(groups recorded, summed device ms) for one kind."""
+    c = ctypes.c_int(0)
+    t = ctypes.c_double(0.0)
+    _check("gbla_prof_read", _lib.load().gbla_prof_read(KERNEL_KINDS.index(kind), ctypes.byref(c),
+                                                         ctypes.byref(t)))
+    return c.value, t.value

@@ -6,8 +6,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <unordered_map>
+#include <vector>
 
 #include "internal.h"
 
@@ -55,6 +57,55 @@ cudaError_t ensure_dyn_smem_ptr(const void* func, size_t bytes) {
   return e;
 }
 
+// ---- instrumentation ---------------------------------------------------------
+static std::atomic<uint64_t> g_launches{0};
+void count_launch(int k) { g_launches.fetch_add((uint64_t)k, std::memory_order_relaxed); }
+
+struct ProfRec {
+  int kind;
+  cudaEvent_t a, b;
+};
+static std::mutex g_prof_mu;
+static unsigned g_prof_mask = 0;
+static std::vector<ProfRec> g_prof_recs;   // recorded pairs, in order
+static std::vector<cudaEvent_t> g_prof_pool;
+static size_t g_prof_open = (size_t)-1;
+
+static cudaEvent_t prof_event() {
+  if (!g_prof_pool.empty()) {
+    cudaEvent_t e = g_prof_pool.back();
+    g_prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void prof_begin(int kind, cudaStream_t s) {
+  if (!(g_prof_mask & (1u << kind))) return;
+  std::lock_guard<std::mutex> lock(g_prof_mu);
+  ProfRec r{kind, prof_event(), prof_event()};
+  cudaEventRecord(r.a, s);
+  g_prof_recs.push_back(r);
+  g_prof_open = g_prof_recs.size() - 1;
+}
+
+void prof_end(int kind, cudaStream_t s) {
+  if (!(g_prof_mask & (1u << kind))) return;
+  std::lock_guard<std::mutex> lock(g_prof_mu);
+  if (g_prof_open < g_prof_recs.size() && g_prof_recs[g_prof_open].kind == kind)
+    cudaEventRecord(g_prof_recs[g_prof_open].b, s);
+  g_prof_open = (size_t)-1;
+}
+
+#define PROF(kind, stream, call)   \
+  do {                             \
+    prof_begin((kind), (stream));  \
+    e = (call);                    \
+    prof_end((kind), (stream));    \
+  } while (0)
+
 static thread_local char g_last_error[256] = "";
 
 static void clear_error() { g_last_error[0] = 0; }
@@ -71,6 +122,17 @@ static int cuda_status_at(cudaError_t e, const char* what, int line) {
   return GBLA_ERR_CUDA;
 }
 #define cuda_status(e) cuda_status_at((e), #e, __LINE__)
+
+#define GBLA_TRYK(kind, stream, expr)      \
+  do {                                     \
+    prof_begin((kind), (stream));          \
+    cudaError_t _e = (expr);               \
+    prof_end((kind), (stream));            \
+    if (_e != cudaSuccess) {               \
+      record_error(_e, #expr, __LINE__);   \
+      return GBLA_ERR_CUDA;                \
+    }                                      \
+  } while (0)
 
 #define GBLA_TRY(expr)                                   \
   do {                                                   \
@@ -140,47 +202,47 @@ static cudaError_t blocked_lu(int n, Ts* A, int lda, int* ipiv, int* info, int n
     const int kb = std::min(nb, n - k0);
     for (int j0 = k0; j0 < k0 + kb; j0 += kPanelWidth) {
       const int jb = std::min(kPanelWidth, k0 + kb - j0);
-      e = launch_panel<Ts>(A + j0 + (size_t)j0 * lda, lda, n - j0, jb, j0, ipiv + j0, info,
-                           w.slots, w.counters + j0 / kPanelWidth, s);
+      PROF(KK_PANEL, s, launch_panel<Ts>(A + j0 + (size_t)j0 * lda, lda, n - j0, jb, j0, ipiv + j0, info,
+                                         w.slots, w.counters + j0 / kPanelWidth, s));
       if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
-      e = launch_laswp<Ts>(A, lda, n, k0, j0, j0 + jb, k0 + kb, ipiv, j0, j0 + jb, s);
+      PROF(KK_LASWP, s, launch_laswp<Ts>(A, lda, n, k0, j0, j0 + jb, k0 + kb, ipiv, j0, j0 + jb, s));
       if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
       const int nrest = k0 + kb - j0 - jb;
       if (nrest > 0) {
-        e = launch_trsm_lunit<Ts, Tc_trsm>(A + j0 + (size_t)j0 * lda, lda,
+        PROF(KK_TRSM, s, (launch_trsm_lunit<Ts, Tc_trsm>(A + j0 + (size_t)j0 * lda, lda,
                                            A + j0 + (size_t)(j0 + jb) * lda, lda, jb, nrest, 0,
-                                           nullptr, 0, nullptr, s);
+                                           nullptr, 0, nullptr, s)));
         if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
-        e = launch_gemm_simt<Ts>(n - j0 - jb, nrest, jb, (Ts)-1, A + (j0 + jb) + (size_t)j0 * lda,
+        PROF(KK_GEMM_SIMT, s, launch_gemm_simt<Ts>(n - j0 - jb, nrest, jb, (Ts)-1, A + (j0 + jb) + (size_t)j0 * lda,
                                  lda, A + j0 + (size_t)(j0 + jb) * lda, lda, false, (Ts)1,
-                                 A + (j0 + jb) + (size_t)(j0 + jb) * lda, lda, false, s);
+                                 A + (j0 + jb) + (size_t)(j0 + jb) * lda, lda, false, s));
         if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
       }
     }
-    e = launch_laswp<Ts>(A, lda, n, 0, k0, k0 + kb, n, ipiv, k0, k0 + kb, s);
+    PROF(KK_LASWP, s, launch_laswp<Ts>(A, lda, n, 0, k0, k0 + kb, n, ipiv, k0, k0 + kb, s));
     if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
     const int nt = n - k0 - kb;
     if (nt <= 0) continue;
     const bool tensor = prec_is_tensor(prec);
-    e = launch_trsm_lunit<Ts, Tc_trsm>(A + k0 + (size_t)k0 * lda, lda, A + k0 + (size_t)(k0 + kb) * lda,
-                                       lda, kb, nt, tensor ? prec : 0, w.Bk, w.ldk, w.eB, s);
+    PROF(KK_TRSM, s, (launch_trsm_lunit<Ts, Tc_trsm>(A + k0 + (size_t)k0 * lda, lda, A + k0 + (size_t)(k0 + kb) * lda,
+                                       lda, kb, nt, tensor ? prec : 0, w.Bk, w.ldk, w.eB, s)));
     if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
     if (tensor) {
       if constexpr (sizeof(Ts) == 4) {
-        e = launch_convert_rows(reinterpret_cast<const float*>(A + (k0 + kb) + (size_t)k0 * lda), lda,
-                                nt, kb, prec, w.Ak, w.ldk, w.eA, s);
+        PROF(KK_CONVERT, s, launch_convert_rows(reinterpret_cast<const float*>(A + (k0 + kb) + (size_t)k0 * lda), lda,
+                                nt, kb, prec, w.Ak, w.ldk, w.eA, s));
         if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
-        e = launch_gemm_tc(prec_mma_kind(prec), nt, nt, prec_kmult(prec) * kb, w.Ak, w.ldk, w.Bk, w.ldk, w.eA, w.eB,
+        PROF(KK_GEMM_TC, s, launch_gemm_tc(prec_mma_kind(prec), nt, nt, prec_kmult(prec) * kb, w.Ak, w.ldk, w.Bk, w.ldk, w.eA, w.eB,
                            reinterpret_cast<float*>(A + (k0 + kb) + (size_t)(k0 + kb) * lda), lda,
-                           info, s);
+                           info, s));
         if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
       } else {
         return cudaErrorInvalidValue;
       }
     } else {
-      e = launch_gemm_simt<Ts>(nt, nt, kb, (Ts)-1, A + (k0 + kb) + (size_t)k0 * lda, lda,
+      PROF(KK_GEMM_SIMT, s, launch_gemm_simt<Ts>(nt, nt, kb, (Ts)-1, A + (k0 + kb) + (size_t)k0 * lda, lda,
                                A + k0 + (size_t)(k0 + kb) * lda, lda, false, (Ts)1,
-                               A + (k0 + kb) + (size_t)(k0 + kb) * lda, lda, false, s);
+                               A + (k0 + kb) + (size_t)(k0 + kb) * lda, lda, false, s));
       if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
     }
   }
@@ -211,6 +273,50 @@ const char* gbla_status_string(int status) {
 }
 
 const char* gbla_last_error(void) { return g_last_error; }
+
+uint64_t gbla_launch_count(void) { return g_launches.load(); }
+
+static const char* kKindNames[KK_COUNT] = {"panel", "laswp",  "trsm", "gemm_simt", "gemm_tc", "convert",
+                                           "trsv",  "matvec", "mgs",  "gmres_update", "permute", "copy"};
+
+const char* gbla_kernel_kind_name(int kind) {
+  return (kind >= 0 && kind < KK_COUNT) ? kKindNames[kind] : "";
+}
+
+void gbla_prof_enable(unsigned mask) {
+  std::lock_guard<std::mutex> lock(g_prof_mu);
+  g_prof_mask = mask;
+}
+
+void gbla_prof_reset(void) {
+  std::lock_guard<std::mutex> lock(g_prof_mu);
+  for (auto& r : g_prof_recs) {
+    g_prof_pool.push_back(r.a);
+    g_prof_pool.push_back(r.b);
+  }
+  g_prof_recs.clear();
+  g_prof_open = (size_t)-1;
+}
+
+int gbla_prof_read(int kind, int* count, double* total_ms) {
+  if (kind < 0 || kind >= KK_COUNT) return -1;
+  if (!count) return -2;
+  if (!total_ms) return -3;
+  std::lock_guard<std::mutex> lock(g_prof_mu);
+  int c = 0;
+  double t = 0.0;
+  for (auto& r : g_prof_recs) {
+    if (r.kind != kind) continue;
+    if (cudaEventSynchronize(r.b) != cudaSuccess) return GBLA_ERR_CUDA;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) return GBLA_ERR_CUDA;
+    ++c;
+    t += ms;
+  }
+  *count = c;
+  *total_ms = t;
+  return GBLA_OK;
+}
 
 void gbla_set_wait_timeout_ns(uint64_t ns) { g_wait_ns = ns; }
 uint64_t gbla_get_wait_timeout_ns(void) { return g_wait_ns; }
@@ -281,7 +387,7 @@ int gbla_lu_factor_mixed(int n, const double* A, int lda, float* F, int ldf, int
   GBLA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), s));
   if (n == 0) return GBLA_OK;
   GBLA_TRY(cudaMemsetAsync(w.counters, 0, sizeof(unsigned) * (size_t)(ceil_div(n, kPanelWidth) + 1), s));
-  GBLA_TRY(launch_copy_d2f(A, lda, F, ldf, n, n, s));
+  GBLA_TRYK(KK_COPY, s, launch_copy_d2f(A, lda, F, ldf, n, n, s));
   return cuda_status(blocked_lu<float>(n, F, ldf, ipiv, d_info, nb, prec, w, s));
 }
 
@@ -316,20 +422,20 @@ int gbla_lu_solve(int trans, int n, int nrhs, const double* LU, int lda, const i
   if (!c.ok) return GBLA_ERR_WORKSPACE;
   GBLA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), s));
   if (n == 0 || nrhs == 0) return GBLA_OK;
-  GBLA_TRY(launch_ipiv_to_perm(n, ipiv, perm, s));
+  GBLA_TRYK(KK_PERM, s, launch_ipiv_to_perm(n, ipiv, perm, s));
   const int ldt = n;
   if (!trans) {
-    GBLA_TRY(launch_permute_rows(n, nrhs, perm, false, B, ldb, T, ldt, s));
-    GBLA_TRY(launch_trsv<double>(true, false, true, n, nrhs, LU, lda, T, ldt, flags, d_info, s));
-    GBLA_TRY(launch_trsv<double>(false, false, false, n, nrhs, LU, lda, T, ldt, flags, d_info, s));
+    GBLA_TRYK(KK_PERM, s, launch_permute_rows(n, nrhs, perm, false, B, ldb, T, ldt, s));
+    GBLA_TRYK(KK_TRSV, s, launch_trsv<double>(true, false, true, n, nrhs, LU, lda, T, ldt, flags, d_info, s));
+    GBLA_TRYK(KK_TRSV, s, launch_trsv<double>(false, false, false, n, nrhs, LU, lda, T, ldt, flags, d_info, s));
     GBLA_TRY(cudaMemcpy2DAsync(B, sizeof(double) * ldb, T, sizeof(double) * ldt, sizeof(double) * n,
                                nrhs, cudaMemcpyDeviceToDevice, s));
   } else {
     GBLA_TRY(cudaMemcpy2DAsync(T, sizeof(double) * ldt, B, sizeof(double) * ldb, sizeof(double) * n,
                                nrhs, cudaMemcpyDeviceToDevice, s));
-    GBLA_TRY(launch_trsv<double>(false, true, false, n, nrhs, LU, lda, T, ldt, flags, d_info, s));
-    GBLA_TRY(launch_trsv<double>(true, true, true, n, nrhs, LU, lda, T, ldt, flags, d_info, s));
-    GBLA_TRY(launch_permute_rows(n, nrhs, perm, true, T, ldt, B, ldb, s));
+    GBLA_TRYK(KK_TRSV, s, launch_trsv<double>(false, true, false, n, nrhs, LU, lda, T, ldt, flags, d_info, s));
+    GBLA_TRYK(KK_TRSV, s, launch_trsv<double>(true, true, true, n, nrhs, LU, lda, T, ldt, flags, d_info, s));
+    GBLA_TRYK(KK_PERM, s, launch_permute_rows(n, nrhs, perm, true, T, ldt, B, ldb, s));
   }
   return GBLA_OK;
 }
@@ -366,9 +472,9 @@ int gbla_backward_error(int n, int nrhs, const double* A, int lda, const double*
   if (!c.ok) return GBLA_ERR_WORKSPACE;
   if (nrhs == 0) return GBLA_OK;
   if (n == 0) return cuda_status(cudaMemsetAsync(d_beta, 0, sizeof(double) * nrhs, s));
-  GBLA_TRY(launch_row_abs_sum_max(n, A, lda, part, anorm, s));
-  GBLA_TRY(launch_residual(n, nrhs, A, lda, X, ldx, B, ldb, R, n, part, s));
-  GBLA_TRY(launch_backward_error_finish(n, nrhs, R, n, X, ldx, anorm, d_beta, s));
+  GBLA_TRYK(KK_MATVEC, s, launch_row_abs_sum_max(n, A, lda, part, anorm, s));
+  GBLA_TRYK(KK_MATVEC, s, launch_residual(n, nrhs, A, lda, X, ldx, B, ldb, R, n, part, s));
+  GBLA_TRYK(KK_MATVEC, s, launch_backward_error_finish(n, nrhs, R, n, X, ldx, anorm, d_beta, s));
   return GBLA_OK;
 }
 
@@ -427,11 +533,13 @@ size_t gbla_gmresir_workspace(int n, int restart_m) {
 // v <- M^{-1} v with M = P^t L U (FP32 factors, FP64 arithmetic); tmp: n doubles
 static cudaError_t apply_minv(int n, const float* F, int ldf, const int* perm, const double* src,
                               double* dst, unsigned* flags, int* info, cudaStream_t s) {
-  cudaError_t e = launch_permute_rows(n, 1, perm, false, src, n, dst, n, s);
+  cudaError_t e;
+  PROF(KK_PERM, s, launch_permute_rows(n, 1, perm, false, src, n, dst, n, s));
   if (e != cudaSuccess) return e;
-  e = launch_trsv<float>(true, false, true, n, 1, F, ldf, dst, n, flags, info, s);
+  PROF(KK_TRSV, s, launch_trsv<float>(true, false, true, n, 1, F, ldf, dst, n, flags, info, s));
   if (e != cudaSuccess) return e;
-  return launch_trsv<float>(false, false, false, n, 1, F, ldf, dst, n, flags, info, s);
+  PROF(KK_TRSV, s, launch_trsv<float>(false, false, false, n, 1, F, ldf, dst, n, flags, info, s));
+  return e;
 }
 
 static int read_scalar(double* host, const double* dev, const int* d_info, cudaStream_t s) {
@@ -476,13 +584,13 @@ int gbla_gmresir_solve(int n, const double* A, int lda, const float* F, int ldf,
   const DeviceProps& dp = device_props();
   if (!dp.coop) return GBLA_ERR_DEVICE;
   GBLA_TRY(cudaMemsetAsync(w.info, 0, sizeof(int), s));
-  GBLA_TRY(launch_ipiv_to_perm(n, ipiv, w.perm, s));
-  GBLA_TRY(launch_row_abs_sum_max(n, A, lda, w.part, w.anorm, s));
+  GBLA_TRYK(KK_PERM, s, launch_ipiv_to_perm(n, ipiv, w.perm, s));
+  GBLA_TRYK(KK_MATVEC, s, launch_row_abs_sum_max(n, A, lda, w.part, w.anorm, s));
   GBLA_TRY(apply_minv(n, F, ldf, w.perm, b, x, w.flags, w.info, s));
   int rc = GBLA_OK;
   for (int outer = 0;; ++outer) {
-    GBLA_TRY(launch_residual(n, 1, A, lda, x, n, b, n, w.r, n, w.part, s));
-    GBLA_TRY(launch_backward_error_finish(n, 1, w.r, n, x, n, w.anorm, w.beta, s));
+    GBLA_TRYK(KK_MATVEC, s, launch_residual(n, 1, A, lda, x, n, b, n, w.r, n, w.part, s));
+    GBLA_TRYK(KK_MATVEC, s, launch_backward_error_finish(n, 1, w.r, n, x, n, w.anorm, w.beta, s));
     double beta = 0.0;
     rc = read_scalar(&beta, w.beta, w.info, s);
     if (rc != GBLA_OK) return rc;
@@ -496,7 +604,7 @@ int gbla_gmresir_solve(int n, const double* A, int lda, const float* F, int ldf,
     if (outer >= opts->max_outer) return GBLA_ERR_NOT_CONVERGED;
     // z = M^{-1} r, v_0 = z / ||z||
     GBLA_TRY(apply_minv(n, F, ldf, w.perm, w.r, w.w, w.flags, w.info, s));
-    GBLA_TRY(launch_mgs_step(n, -1, w.V, w.ldv, w.w, w.H, m + 1, w.cs, w.sn, w.g, w.st, w.slots,
+    GBLA_TRYK(KK_MGS, s, launch_mgs_step(n, -1, w.V, w.ldv, w.w, w.H, m + 1, w.cs, w.sn, w.g, w.st, w.slots,
                              w.counter, w.info, s));
     double beta_in = 0.0;
     rc = read_scalar(&beta_in, w.st, w.info, s);
@@ -508,9 +616,9 @@ int gbla_gmresir_solve(int n, const double* A, int lda, const float* F, int ldf,
     int k = 0;
     for (int j = 0; j < m; ++j) {
       // w = M^{-1} A v_j
-      GBLA_TRY(launch_residual(n, 1, A, lda, w.V + (size_t)j * w.ldv, n, nullptr, n, w.w, n, w.part, s));
+      GBLA_TRYK(KK_MATVEC, s, launch_residual(n, 1, A, lda, w.V + (size_t)j * w.ldv, n, nullptr, n, w.w, n, w.part, s));
       GBLA_TRY(apply_minv(n, F, ldf, w.perm, w.w, w.r, w.flags, w.info, s));
-      GBLA_TRY(launch_mgs_step(n, j, w.V, w.ldv, w.r, w.H, m + 1, w.cs, w.sn, w.g, w.st, w.slots,
+      GBLA_TRYK(KK_MGS, s, launch_mgs_step(n, j, w.V, w.ldv, w.r, w.H, m + 1, w.cs, w.sn, w.g, w.st, w.slots,
                                w.counter, w.info, s));
       double res = 0.0;
       rc = read_scalar(&res, w.st, w.info, s);
@@ -519,7 +627,7 @@ int gbla_gmresir_solve(int n, const double* A, int lda, const float* F, int ldf,
       if (res <= opts->inner_tol * beta_in) break;
     }
     stats->inner += k;
-    GBLA_TRY(launch_gmres_update(n, k, w.V, w.ldv, w.H, m + 1, w.g, x, s));
+    GBLA_TRYK(KK_UPDATE, s, launch_gmres_update(n, k, w.V, w.ldv, w.H, m + 1, w.g, x, s));
   }
 }
 

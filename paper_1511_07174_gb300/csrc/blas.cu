@@ -46,6 +46,7 @@ cudaError_t launch_laswp(T* A, int lda, int nrows, int c0, int c1, int c2, int c
   const int threads = 128;
   laswp_kernel<T><<<(ncols + threads - 1) / threads, threads, 0, s>>>(A, lda, nrows, c0, c1, c2, c3,
                                                                      ipiv, k1, k2);
+  count_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_laswp<double>(double*, int, int, int, int, int, int, const int*, int,
@@ -207,6 +208,7 @@ cudaError_t launch_trsm_lunit(const Ts* L, int ldl, Ts* B, int ldb, int w, int N
     default: return cudaErrorInvalidValue;
   }
 #undef GBLA_TRSM_CASE
+  count_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_trsm_lunit<double, double>(const double*, int, double*, int, int, int,
@@ -320,6 +322,7 @@ cudaError_t launch_gemm_simt(int M, int N, int K, T alpha, const T* A, int lda, 
           M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
     }
   }
+  count_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_gemm_simt<double>(int, int, int, double, const double*, int,
@@ -400,6 +403,7 @@ cudaError_t launch_convert_rows(const float* F, int ldf, int M, int K, int kind,
     default:
       return cudaErrorInvalidValue;
   }
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -420,6 +424,7 @@ cudaError_t launch_copy_d2f(const double* A, int lda, float* F, int ldf, int m, 
     const int nc = n - c0 < 65535 ? n - c0 : 65535;
     copy_d2f_kernel<<<dim3(bx, nc), 256, 0, s>>>(A + (size_t)c0 * lda, lda, F + (size_t)c0 * ldf,
                                                  ldf, m, nc);
+    count_launch();
   }
   return cudaGetLastError();
 }
@@ -458,6 +463,7 @@ cudaError_t launch_ipiv_to_perm(int n, const int* ipiv, int* perm, cudaStream_t 
     if (ea != cudaSuccess) return ea;
   }
   ipiv_to_perm_kernel<<<1, 1024, use_smem ? bytes : 0, s>>>(n, ipiv, perm, use_smem);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -481,6 +487,7 @@ cudaError_t launch_permute_rows(int n, int nrhs, const int* perm, bool inverse, 
   if (bx > 1024) bx = 1024;
   permute_rows_kernel<<<dim3(bx, nrhs), 256, 0, s>>>(n, nrhs, perm, inverse ? 1 : 0, src, lds, dst,
                                                      ldd);
+  count_launch();
   return cudaGetLastError();
 }
 

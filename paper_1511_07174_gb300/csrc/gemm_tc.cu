@@ -328,6 +328,7 @@ cudaError_t launch_gemm_tc(int kind, int M, int N, int K, const void* Ak, int ld
     default:
       return cudaErrorInvalidValue;
   }
+  count_launch();
   return cudaGetLastError();
 }
 

@@ -52,6 +52,27 @@ struct Carver {
   }
 };
 
+// ---- instrumentation -----------------------------------------------------------
+// Kernel groups that can be bracketed with CUDA events (gbla_prof_*).
+enum KernelKind {
+  KK_PANEL = 0,
+  KK_LASWP,
+  KK_TRSM,
+  KK_GEMM_SIMT,
+  KK_GEMM_TC,
+  KK_CONVERT,
+  KK_TRSV,
+  KK_MATVEC,
+  KK_MGS,
+  KK_UPDATE,
+  KK_PERM,
+  KK_COPY,
+  KK_COUNT
+};
+void count_launch(int k = 1);                 // every kernel launch of the library
+void prof_begin(int kind, cudaStream_t s);    // no-op unless the kind is enabled
+void prof_end(int kind, cudaStream_t s);
+
 // ---- precision kinds of the mixed trailing update ---------------------------
 inline bool prec_is_tensor(int p) { return p >= GBLA_PREC_TF32 && p <= GBLA_PREC_BF16X3; }
 inline bool prec_is_split(int p) { return p == GBLA_PREC_FP16X3 || p == GBLA_PREC_BF16X3; }

@@ -80,6 +80,7 @@ cudaError_t launch_residual(int n, int nrhs, const double* A, int lda, const dou
     if (bx > 512) bx = 512;
     residual_finish_kernel<<<dim3(bx, nc), 256, 0, s>>>(
         n, nc, chunks, work, B ? B + (size_t)c0 * ldb : nullptr, ldb, R + (size_t)c0 * ldr, ldr);
+    count_launch(2);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -112,6 +113,7 @@ cudaError_t launch_row_abs_sum_max(int n, const double* A, int lda, double* work
   dim3 grid((n + kResRows - 1) / kResRows, chunks);
   matvec_partial_kernel<true><<<grid, kResRows, 0, s>>>(n, 1, A, lda, nullptr, 0, work);
   rowsum_max_kernel<<<1, 1024, 0, s>>>(n, chunks, work, anorm);
+  count_launch(2);
   return cudaGetLastError();
 }
 
@@ -150,6 +152,7 @@ cudaError_t launch_backward_error_finish(int n, int nrhs, const double* R, int l
                                          cudaStream_t s) {
   if (nrhs <= 0) return cudaSuccess;
   backward_error_finish_kernel<<<nrhs, 1024, 0, s>>>(n, R, ldr, X, ldx, anorm, beta);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -284,6 +287,7 @@ cudaError_t launch_mgs_step(int n, int j, double* V, int ldv, const double* w, d
   GmresState* stp = static_cast<GmresState*>(st);
   uint64_t wait_ns = wait_timeout_ns();
   void* args[] = {&n, &j, &ldv, &V, &w, &H, &ldh, &cs, &sn, &g, &stp, &slots, &counter, &info, &wait_ns};
+  count_launch();
   return cudaLaunchCooperativeKernel((const void*)mgs_step_kernel, dim3(C), dim3(kMgsThreads), args,
                                      smem, s);
 }
@@ -323,6 +327,7 @@ cudaError_t launch_gmres_update(int n, int k, const double* V, int ldv, const do
   int bx = (n + 255) / 256;
   if (bx > 1024) bx = 1024;
   gmres_update_kernel<<<bx, 256, 0, s>>>(n, k, V, ldv, H, ldh, g, x);
+  count_launch();
   return cudaGetLastError();
 }
 

@@ -202,6 +202,7 @@ cudaError_t launch_panel(Ts* A, int lda, int m, int w, int row0, int* ipiv, int*
   if (ea != cudaSuccess) return ea;
   uint64_t wait_ns = wait_timeout_ns();
   void* args[] = {&A, &lda, &m, &w, &row0, &R, &ipiv, &info, &slots, &counter, &wait_ns};
+  count_launch();
   return cudaLaunchCooperativeKernel((const void*)panel_kernel<Ts>, dim3(C), dim3(kPanelThreads),
                                      args, smem, s);
 }

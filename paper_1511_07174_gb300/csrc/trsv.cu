@@ -176,6 +176,7 @@ cudaError_t launch_trsv(bool lower, bool trans, bool unit, int n, int nrhs, cons
     else if (!lower && trans && unit) GBLA_TRSV(false, true, true);
     else GBLA_TRSV(false, true, false);
 #undef GBLA_TRSV
+    count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
