@@ -203,7 +203,7 @@ static cudaError_t blocked_lu(int n, Ts* A, int lda, int* ipiv, int* info, int n
     for (int j0 = k0; j0 < k0 + kb; j0 += kPanelWidth) {
       const int jb = std::min(kPanelWidth, k0 + kb - j0);
       PROF(KK_PANEL, s, launch_panel<Ts>(A + j0 + (size_t)j0 * lda, lda, n - j0, jb, j0, ipiv + j0, info,
-                                         w.slots, w.counters + j0 / kPanelWidth, s));
+                                         w.slots, (unsigned)(j0 / kPanelWidth), s));
       if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
       PROF(KK_LASWP, s, launch_laswp<Ts>(A, lda, n, k0, j0, j0 + jb, k0 + kb, ipiv, j0, j0 + jb, s));
       if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
@@ -350,7 +350,7 @@ int gbla_lu_factor(int n, double* A, int lda, int* ipiv, int* d_info, int nb, vo
   if (!dp.coop) return GBLA_ERR_DEVICE;
   GBLA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), s));
   if (n == 0) return GBLA_OK;
-  GBLA_TRY(cudaMemsetAsync(w.counters, 0, sizeof(unsigned) * (size_t)(ceil_div(n, kPanelWidth) + 1), s));
+  GBLA_TRY(cudaMemsetAsync(w.slots, 0, sizeof(double) * panel_slots_doubles(), s));
   return cuda_status(blocked_lu<double>(n, A, lda, ipiv, d_info, nb, 0, w, s));
 }
 
@@ -386,7 +386,7 @@ int gbla_lu_factor_mixed(int n, const double* A, int lda, float* F, int ldf, int
   if (!dp.coop) return GBLA_ERR_DEVICE;
   GBLA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), s));
   if (n == 0) return GBLA_OK;
-  GBLA_TRY(cudaMemsetAsync(w.counters, 0, sizeof(unsigned) * (size_t)(ceil_div(n, kPanelWidth) + 1), s));
+  GBLA_TRY(cudaMemsetAsync(w.slots, 0, sizeof(double) * panel_slots_doubles(), s));
   GBLA_TRYK(KK_COPY, s, launch_copy_d2f(A, lda, F, ldf, n, n, s));
   return cuda_status(blocked_lu<float>(n, F, ldf, ipiv, d_info, nb, prec, w, s));
 }
@@ -493,6 +493,8 @@ struct IrWork {
   double* slots;
   unsigned* counter;
   unsigned* flags;
+  double* DinvL;
+  double* DinvU;
   int* info;
   double* anorm;
   double* beta;
@@ -516,6 +518,8 @@ static size_t ir_layout(Carver& c, int n, int m, IrWork* w) {
   t.slots = c.take<double>(mgs_slots_doubles());
   t.counter = c.take<unsigned>(1);
   t.flags = c.take<unsigned>(trsv_flags_count(nn));
+  t.DinvL = c.take<double>(diag_inv_doubles(nn));
+  t.DinvU = c.take<double>(diag_inv_doubles(nn));
   t.info = c.take<int>(1);
   t.anorm = c.take<double>(1);
   t.beta = c.take<double>(1);
@@ -530,15 +534,17 @@ size_t gbla_gmresir_workspace(int n, int restart_m) {
   return ir_layout(c, n, restart_m, nullptr);
 }
 
-// v <- M^{-1} v with M = P^t L U (FP32 factors, FP64 arithmetic); tmp: n doubles
-static cudaError_t apply_minv(int n, const float* F, int ldf, const int* perm, const double* src,
-                              double* dst, unsigned* flags, int* info, cudaStream_t s) {
+// dst <- M^{-1} src with M = P^t L U (FP32 factors, FP64 arithmetic, inverted
+// 64 x 64 diagonal blocks of L and U formed once per solve call)
+static cudaError_t apply_minv(int n, const float* F, int ldf, const int* perm, const double* DinvL,
+                              const double* DinvU, const double* src, double* dst, unsigned* flags,
+                              int* info, cudaStream_t s) {
   cudaError_t e;
   PROF(KK_PERM, s, launch_permute_rows(n, 1, perm, false, src, n, dst, n, s));
   if (e != cudaSuccess) return e;
-  PROF(KK_TRSV, s, launch_trsv<float>(true, false, true, n, 1, F, ldf, dst, n, flags, info, s));
+  PROF(KK_TRSV, s, launch_trsv_inv<float>(true, n, F, ldf, DinvL, dst, flags, info, s));
   if (e != cudaSuccess) return e;
-  PROF(KK_TRSV, s, launch_trsv<float>(false, false, false, n, 1, F, ldf, dst, n, flags, info, s));
+  PROF(KK_TRSV, s, launch_trsv_inv<float>(false, n, F, ldf, DinvU, dst, flags, info, s));
   return e;
 }
 
@@ -585,8 +591,10 @@ int gbla_gmresir_solve(int n, const double* A, int lda, const float* F, int ldf,
   if (!dp.coop) return GBLA_ERR_DEVICE;
   GBLA_TRY(cudaMemsetAsync(w.info, 0, sizeof(int), s));
   GBLA_TRYK(KK_PERM, s, launch_ipiv_to_perm(n, ipiv, w.perm, s));
+  GBLA_TRYK(KK_TRSV, s, launch_diag_inv<float>(true, true, n, F, ldf, w.DinvL, s));
+  GBLA_TRYK(KK_TRSV, s, launch_diag_inv<float>(false, false, n, F, ldf, w.DinvU, s));
   GBLA_TRYK(KK_MATVEC, s, launch_row_abs_sum_max(n, A, lda, w.part, w.anorm, s));
-  GBLA_TRY(apply_minv(n, F, ldf, w.perm, b, x, w.flags, w.info, s));
+  GBLA_TRY(apply_minv(n, F, ldf, w.perm, w.DinvL, w.DinvU, b, x, w.flags, w.info, s));
   int rc = GBLA_OK;
   for (int outer = 0;; ++outer) {
     GBLA_TRYK(KK_MATVEC, s, launch_residual(n, 1, A, lda, x, n, b, n, w.r, n, w.part, s));
@@ -603,7 +611,7 @@ int gbla_gmresir_solve(int n, const double* A, int lda, const float* F, int ldf,
     }
     if (outer >= opts->max_outer) return GBLA_ERR_NOT_CONVERGED;
     // z = M^{-1} r, v_0 = z / ||z||
-    GBLA_TRY(apply_minv(n, F, ldf, w.perm, w.r, w.w, w.flags, w.info, s));
+    GBLA_TRY(apply_minv(n, F, ldf, w.perm, w.DinvL, w.DinvU, w.r, w.w, w.flags, w.info, s));
     GBLA_TRYK(KK_MGS, s, launch_mgs_step(n, -1, w.V, w.ldv, w.w, w.H, m + 1, w.cs, w.sn, w.g, w.st, w.slots,
                              w.counter, w.info, s));
     double beta_in = 0.0;
@@ -617,7 +625,7 @@ int gbla_gmresir_solve(int n, const double* A, int lda, const float* F, int ldf,
     for (int j = 0; j < m; ++j) {
       // w = M^{-1} A v_j
       GBLA_TRYK(KK_MATVEC, s, launch_residual(n, 1, A, lda, w.V + (size_t)j * w.ldv, n, nullptr, n, w.w, n, w.part, s));
-      GBLA_TRY(apply_minv(n, F, ldf, w.perm, w.w, w.r, w.flags, w.info, s));
+      GBLA_TRY(apply_minv(n, F, ldf, w.perm, w.DinvL, w.DinvU, w.w, w.r, w.flags, w.info, s));
       GBLA_TRYK(KK_MGS, s, launch_mgs_step(n, j, w.V, w.ldv, w.r, w.H, m + 1, w.cs, w.sn, w.g, w.st, w.slots,
                                w.counter, w.info, s));
       double res = 0.0;

@@ -11,7 +11,10 @@
 //   warps 0..3     -- epilogue: tcgen05.ld of the warp's 32 TMEM lanes, then
 //                     C[row, col] -= D * 2^-eA[row] * 2^-eB[col] on the FP32
 //                     working matrix (column-major; a warp covers 32
-//                     consecutive rows, so every access is one 128-byte line).
+//                     consecutive rows, so every access is one 128-byte line;
+//                     32 columns are loaded before any is stored).
+// Shared memory (3 stages, ~97 KB) and tensor memory (128 columns) leave room
+// for two CTAs per SM, so one CTA's epilogue overlaps the other's MMAs.
 // Every mbarrier wait is bounded; a wait that gives up records
 // GBLA_INFO_TIMEOUT, skips the epilogue writes, drains the copies it issued and
 // frees its tensor memory before returning.
@@ -22,7 +25,7 @@
 
 namespace gbla {
 
-constexpr int kTcBM = 128, kTcBN = 128, kTcStages = 4;
+constexpr int kTcBM = 128, kTcBN = 128, kTcStages = 3;  // 3 stages: two CTAs fit per SM
 constexpr int kTcStageBytes = 128 * 128;  // one operand tile: 128 rows x 128 bytes
 constexpr int kTcSmemBytes = 2 * kTcStages * kTcStageBytes + 1024 /*align*/ + 256 /*barriers*/;
 
@@ -137,7 +140,7 @@ struct TcArgs {
 };
 
 template <int KIND>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(128, 2)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    TcArgs args) {
   extern __shared__ unsigned char smraw[];
@@ -153,6 +156,7 @@ __global__ void __launch_bounds__(128, 1)
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * kTcStages + 1);
   int* s_fail = reinterpret_cast<int*>(tmem_holder + 1);
   int* s_issued = s_fail + 1;
+  __shared__ float s_sb[kTcBN];  // 2^-eB of the tile's columns
 
   constexpr int kElem = (KIND == GBLA_PREC_TF32) ? 4 : 2;
   constexpr int kBK = 128 / kElem;  // elements per 128-byte row
@@ -163,6 +167,10 @@ __global__ void __launch_bounds__(128, 1)
   const int m0 = blockIdx.x * kTcBM, n0 = blockIdx.y * kTcBN;
   const int KB = (args.K + kBK - 1) / kBK;
 
+  for (int c = threadIdx.x; c < kTcBN; c += blockDim.x) {
+    const int col = n0 + c;
+    s_sb[c] = (args.eB && col < args.N) ? pow2f(-args.eB[col]) : 1.0f;
+  }
   if (threadIdx.x == 0) {
     for (int s = 0; s < kTcStages; ++s) {
       mbar_init(bar_full + 8 * s, 1);
@@ -237,21 +245,21 @@ __global__ void __launch_bounds__(128, 1)
     const int row = m0 + warp * 32 + lane;
     const bool rok = row < args.M;
     const float sa = (rok && args.eA) ? pow2f(-args.eA[row]) : 1.0f;
-    float* crow = args.C + row;
+    float* __restrict__ crow = args.C + row + (size_t)n0 * args.ldc;
+    const int ncol = min(kTcBN, args.N - n0);
 #pragma unroll 1
     for (int cb = 0; cb < kTcBN; cb += 32) {
       uint32_t v[32];
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
       if (rok) {
+        float cv[32];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int col = n0 + cb + j;
-          if (col < args.N) {
-            const float sb = args.eB ? pow2f(-__ldg(args.eB + col)) : 1.0f;
-            float* c = crow + (size_t)col * args.ldc;
-            *c = *c - (__uint_as_float(v[j]) * sa) * sb;
-          }
-        }
+        for (int j = 0; j < 32; ++j)
+          cv[j] = (cb + j < ncol) ? crow[(size_t)(cb + j) * args.ldc] : 0.0f;
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (cb + j < ncol)
+            crow[(size_t)(cb + j) * args.ldc] = cv[j] - (__uint_as_float(v[j]) * sa) * s_sb[cb + j];
       }
     }
   }

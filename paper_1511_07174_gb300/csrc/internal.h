@@ -87,12 +87,14 @@ inline int prec_kmult(int p) { return prec_is_split(p) ? 3 : 1; }
 constexpr int kPanelWidth = 32;  // inner panel width handled by the cooperative kernel
 constexpr int kPanelSlotW = 72;  // doubles per published candidate slot
 
-// Workspace for one panel launch: 2 * (num_sms + 1) slots + counters.
+// Exchange slots of the panel kernel: 2 * (num_sms + 1) slots. They must be
+// zeroed once before the first panel of a factorisation; panel_index (distinct
+// for every panel of one factorisation, < 2^25) tags the slot headers.
 size_t panel_slots_doubles();
 
 template <typename Ts>
 cudaError_t launch_panel(Ts* A, int lda, int m, int w, int row0, int* ipiv, int* info,
-                         double* slots, unsigned* counter, cudaStream_t s);
+                         double* slots, unsigned panel_index, cudaStream_t s);
 
 // Interchanges ipiv[k1..k2) on columns [c0,c1) u [c2,c3); rows outside
 // [k, nrows) named by a pivot are ignored (defensive: never index out of A).
@@ -135,6 +137,16 @@ template <typename Ts>
 cudaError_t launch_trsv(bool lower, bool trans, bool unit, int n, int nrhs, const Ts* T, int ldt,
                         double* X, int ldx, unsigned* flags, int* info, cudaStream_t s);
 size_t trsv_flags_count(int n);
+
+// Preconditioner apply with inverted 64 x 64 diagonal blocks (one RHS).
+// Dinv holds diag_inv_doubles(n) doubles per triangular factor.
+size_t diag_inv_doubles(int n);
+template <typename Ts>
+cudaError_t launch_diag_inv(bool lower, bool unit, int n, const Ts* T, int ldt, double* Dinv,
+                            cudaStream_t s);
+template <typename Ts>
+cudaError_t launch_trsv_inv(bool lower, int n, const Ts* T, int ldt, const double* Dinv, double* X,
+                            unsigned* flags, int* info, cudaStream_t s);
 
 cudaError_t launch_ipiv_to_perm(int n, const int* ipiv, int* perm, cudaStream_t s);
 // dst[i, c] = src[perm[i], c] (forward) or dst[perm[i], c] = src[i, c] (inverse)

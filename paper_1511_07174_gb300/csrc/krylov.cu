@@ -17,41 +17,58 @@ size_t residual_work_doubles(int n, int nrhs) {
   return chunks * (size_t)(n > 0 ? n : 1) * (size_t)(nrhs > 0 ? nrhs : 1);
 }
 
-// part[chunk][c][i] = sum_{j in chunk} A[i, j] X[j, c]   (ABS: |A[i, j]|, X unused)
-template <bool ABS>
+// part[chunk][c][i] = sum_{j in chunk} A[i, j] X[j, c]   (ABS: |A[i, j]|, X unused).
+// NR is the number of right-hand sides of this pass (compile time, so the
+// accumulators stay in registers); two interleaved accumulators per sum keep
+// two independent FMA chains in flight.
+template <bool ABS, int NR>
 __global__ void __launch_bounds__(kResRows)
-    matvec_partial_kernel(int n, int nrhs, const double* __restrict__ A, int lda,
+    matvec_partial_kernel(int n, const double* __restrict__ A, int lda,
                           const double* __restrict__ X, int ldx, double* __restrict__ part) {
-  __shared__ double xs[kResCols][kResNR];
+  __shared__ double xs[kResCols][NR];
   const int i = blockIdx.x * kResRows + threadIdx.x;
   const int chunk = blockIdx.y;
   const int j0 = chunk * kResCols;
   const int nc = min(kResCols, n - j0);
   if (!ABS) {
-    for (int idx = threadIdx.x; idx < kResCols * nrhs; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < kResCols * NR; idx += blockDim.x) {
       const int jj = idx % kResCols, c = idx / kResCols;
       xs[jj][c] = jj < nc ? X[(j0 + jj) + (size_t)c * ldx] : 0.0;
     }
     __syncthreads();
   }
   if (i >= n) return;
-  double acc[kResNR];
+  double acc0[NR], acc1[NR];
 #pragma unroll
-  for (int c = 0; c < kResNR; ++c) acc[c] = 0.0;
+  for (int c = 0; c < NR; ++c) acc0[c] = acc1[c] = 0.0;
   const double* a = A + i + (size_t)j0 * lda;
+  int jj = 0;
 #pragma unroll 4
-  for (int jj = 0; jj < nc; ++jj) {
-    const double v = __ldg(a + (size_t)jj * lda);
+  for (; jj + 1 < nc; jj += 2) {
+    const double v0 = __ldg(a + (size_t)jj * lda);
+    const double v1 = __ldg(a + (size_t)(jj + 1) * lda);
     if (ABS) {
-      acc[0] += fabs(v);
+      acc0[0] += fabs(v0);
+      acc1[0] += fabs(v1);
     } else {
 #pragma unroll
-      for (int c = 0; c < kResNR; ++c)
-        if (c < nrhs) acc[c] = fma(v, xs[jj][c], acc[c]);
+      for (int c = 0; c < NR; ++c) {
+        acc0[c] = fma(v0, xs[jj][c], acc0[c]);
+        acc1[c] = fma(v1, xs[jj + 1][c], acc1[c]);
+      }
     }
   }
-  const int nr = ABS ? 1 : nrhs;
-  for (int c = 0; c < nr; ++c) part[((size_t)chunk * nr + c) * n + i] = acc[c];
+  if (jj < nc) {
+    const double v0 = __ldg(a + (size_t)jj * lda);
+    if (ABS) {
+      acc0[0] += fabs(v0);
+    } else {
+#pragma unroll
+      for (int c = 0; c < NR; ++c) acc0[c] = fma(v0, xs[jj][c], acc0[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NR; ++c) part[((size_t)chunk * NR + c) * n + i] = acc0[c] + acc1[c];
 }
 
 // R[i, c] = B[i, c] - sum_chunk part (or + sum when B == nullptr), fixed order.
@@ -71,11 +88,17 @@ cudaError_t launch_residual(int n, int nrhs, const double* A, int lda, const dou
                             cudaStream_t s) {
   if (n <= 0 || nrhs <= 0) return cudaSuccess;
   const int chunks = (n + kResCols - 1) / kResCols;
-  for (int c0 = 0; c0 < nrhs; c0 += kResNR) {
-    const int nc = nrhs - c0 < kResNR ? nrhs - c0 : kResNR;
+  for (int c0 = 0; c0 < nrhs;) {
+    const int left = nrhs - c0;
+    const int nc = left >= 8 ? 8 : (left >= 4 ? 4 : (left >= 2 ? 2 : 1));
     dim3 grid((n + kResRows - 1) / kResRows, chunks);
-    matvec_partial_kernel<false><<<grid, kResRows, 0, s>>>(n, nc, A, lda, X + (size_t)c0 * ldx,
-                                                           ldx, work);
+    const double* Xc = X + (size_t)c0 * ldx;
+    switch (nc) {
+      case 8: matvec_partial_kernel<false, 8><<<grid, kResRows, 0, s>>>(n, A, lda, Xc, ldx, work); break;
+      case 4: matvec_partial_kernel<false, 4><<<grid, kResRows, 0, s>>>(n, A, lda, Xc, ldx, work); break;
+      case 2: matvec_partial_kernel<false, 2><<<grid, kResRows, 0, s>>>(n, A, lda, Xc, ldx, work); break;
+      default: matvec_partial_kernel<false, 1><<<grid, kResRows, 0, s>>>(n, A, lda, Xc, ldx, work); break;
+    }
     int bx = (n + 255) / 256;
     if (bx > 512) bx = 512;
     residual_finish_kernel<<<dim3(bx, nc), 256, 0, s>>>(
@@ -83,6 +106,7 @@ cudaError_t launch_residual(int n, int nrhs, const double* A, int lda, const dou
     count_launch(2);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    c0 += nc;
   }
   return cudaSuccess;
 }
@@ -111,7 +135,7 @@ cudaError_t launch_row_abs_sum_max(int n, const double* A, int lda, double* work
   if (n <= 0) return cudaMemsetAsync(anorm, 0, sizeof(double), s);
   const int chunks = (n + kResCols - 1) / kResCols;
   dim3 grid((n + kResRows - 1) / kResRows, chunks);
-  matvec_partial_kernel<true><<<grid, kResRows, 0, s>>>(n, 1, A, lda, nullptr, 0, work);
+  matvec_partial_kernel<true, 1><<<grid, kResRows, 0, s>>>(n, A, lda, nullptr, 0, work);
   rowsum_max_kernel<<<1, 1024, 0, s>>>(n, chunks, work, anorm);
   count_launch(2);
   return cudaGetLastError();

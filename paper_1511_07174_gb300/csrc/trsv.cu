@@ -189,3 +189,202 @@ template cudaError_t launch_trsv<float>(bool, bool, bool, int, int, const float*
                                         int, unsigned*, int*, cudaStream_t);
 
 }  // namespace gbla
+
+// ----------------------------------------------------------------------------
+// Substitution with inverted diagonal blocks (the preconditioner apply of the
+// refinement, one right-hand side). The inverse of every 64 x 64 diagonal
+// block of the triangular factor is formed once per factorisation, in FP64,
+// so that the per-block step of the chain is a 64 x 64 matrix-vector product
+// instead of 64 dependent row eliminations. The operator applied is then a
+// fixed linear map (the same for every vector), as GMRES requires.
+namespace gbla {
+
+// Dinv + b*64*64: column-major inverse of diagonal block b (zero-padded when
+// the last block has fewer than 64 rows). One 64-thread CTA per block; thread
+// j forms column j by substitution against e_j.
+template <typename Ts, bool LOWER, bool UNIT>
+__global__ void __launch_bounds__(64)
+    diag_inv_kernel(int n, const Ts* __restrict__ T, int ldt, double* __restrict__ Dinv) {
+  __shared__ double D[kTsBS][kTsBS + 1];
+  const int b = blockIdx.x;
+  const int r0 = b * kTsBS;
+  const int nr = min(kTsBS, n - r0);
+  const int t = threadIdx.x;
+  for (int j = 0; j < kTsBS; ++j) D[t][j] = (t < nr && j < nr) ? (double)T[(r0 + t) + (size_t)(r0 + j) * ldt] : 0.0;
+  __syncthreads();
+  double* out = Dinv + (size_t)b * kTsBS * kTsBS + (size_t)t * kTsBS;  // column t
+  double x[kTsBS];
+#pragma unroll
+  for (int i = 0; i < kTsBS; ++i) x[i] = 0.0;
+  if (t < nr) {
+    if (LOWER) {
+#pragma unroll
+      for (int i = 0; i < kTsBS; ++i) {
+        if (i >= t && i < nr) {
+          double s = (i == t) ? 1.0 : 0.0;
+#pragma unroll
+          for (int k = 0; k < kTsBS; ++k)
+            if (k >= t && k < i) s = fma(-D[i][k], x[k], s);
+          x[i] = UNIT ? s : s / D[i][i];
+        }
+      }
+    } else {
+#pragma unroll
+      for (int ii = kTsBS - 1; ii >= 0; --ii) {
+        if (ii <= t) {
+          double s = (ii == t) ? 1.0 : 0.0;
+#pragma unroll
+          for (int k = 0; k < kTsBS; ++k)
+            if (k > ii && k <= t) s = fma(-D[ii][k], x[k], s);
+          x[ii] = UNIT ? s : s / D[ii][ii];
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < kTsBS; ++i) out[i] = x[i];
+}
+
+template <typename Ts>
+cudaError_t launch_diag_inv(bool lower, bool unit, int n, const Ts* T, int ldt, double* Dinv,
+                            cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int nblk = (n + kTsBS - 1) / kTsBS;
+  if (lower && unit) diag_inv_kernel<Ts, true, true><<<nblk, 64, 0, s>>>(n, T, ldt, Dinv);
+  else if (lower) diag_inv_kernel<Ts, true, false><<<nblk, 64, 0, s>>>(n, T, ldt, Dinv);
+  else if (unit) diag_inv_kernel<Ts, false, true><<<nblk, 64, 0, s>>>(n, T, ldt, Dinv);
+  else diag_inv_kernel<Ts, false, false><<<nblk, 64, 0, s>>>(n, T, ldt, Dinv);
+  count_launch();
+  return cudaGetLastError();
+}
+template cudaError_t launch_diag_inv<float>(bool, bool, int, const float*, int, double*, cudaStream_t);
+template cudaError_t launch_diag_inv<double>(bool, bool, int, const double*, int, double*, cudaStream_t);
+
+size_t diag_inv_doubles(int n) { return (size_t)((n + kTsBS - 1) / kTsBS) * kTsBS * kTsBS; }
+
+// One right-hand side, forward (lower factor) or backward (upper factor).
+// Tiles of earlier blocks are prefetched into registers one step ahead so that
+// their loads overlap the wait for the previous block.
+template <typename Ts, bool FWD>
+__global__ void __launch_bounds__(256)
+    trsv_inv_kernel(int n, const Ts* __restrict__ T, int ldt, const double* __restrict__ Dinv,
+                    double* X, unsigned* flags, int* info, uint64_t wait_ns) {
+  extern __shared__ double smd[];
+  double (*tile)[kTsBS + 1] = reinterpret_cast<double (*)[kTsBS + 1]>(smd);      // 64 x 65
+  double* dinv = smd + kTsBS * (kTsBS + 1);                                       // 64 x 64
+  double* xq = dinv + kTsBS * kTsBS;                                              // 64
+  double* part = xq + kTsBS;                                                      // 4 x 64
+  __shared__ int s_t, s_abort;
+  const int tid = threadIdx.x;
+  const int nblk = (n + kTsBS - 1) / kTsBS;
+  if (tid == 0) {
+    s_t = (int)atomicAdd(&flags[nblk], 1u);
+    s_abort = 0;
+  }
+  __syncthreads();
+  const int t_ord = s_t;
+  if (t_ord >= nblk) return;
+  const int b = FWD ? t_ord : nblk - 1 - t_ord;
+  const int r0 = b * kTsBS;
+  const int nr = min(kTsBS, n - r0);
+  const int r = tid & 63, g = tid >> 6;
+
+  // the inverse of the diagonal block, needed last, is staged first
+  const double* Db = Dinv + (size_t)b * kTsBS * kTsBS;
+  for (int idx = tid; idx < kTsBS * kTsBS; idx += blockDim.x) dinv[idx] = Db[idx];
+
+  Ts pf[16];
+  auto prefetch = [&](int st) {
+    const int q = FWD ? st : nblk - 1 - st;
+    const int c0 = q * kTsBS;
+    const int nc = min(kTsBS, n - c0);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int idx = tid + 256 * i;
+      const int rr = idx & 63, jj = idx >> 6;
+      pf[i] = (rr < nr && jj < nc) ? T[(r0 + rr) + (size_t)(c0 + jj) * ldt] : (Ts)0;
+    }
+  };
+  double a0 = 0.0, a1 = 0.0;
+  if (t_ord > 0) prefetch(0);
+  for (int st = 0; st < t_ord; ++st) {
+    const int q = FWD ? st : nblk - 1 - st;
+    const int c0 = q * kTsBS;
+    const int nc = min(kTsBS, n - c0);
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int idx = tid + 256 * i;
+      tile[idx & 63][idx >> 6] = (double)pf[i];
+    }
+    if (st + 1 < t_ord) prefetch(st + 1);
+    if (tid == 0) {
+      if (!gbla_wait_geq(&flags[q], 1u, wait_ns)) {
+        gbla_flag_timeout(info);
+        s_abort = 1;
+      }
+      __threadfence();
+    }
+    __syncthreads();
+    if (s_abort) return;
+    if (tid < kTsBS) xq[tid] = tid < nc ? __ldcg(&X[c0 + tid]) : 0.0;
+    __syncthreads();
+#pragma unroll
+    for (int jj = g * 16; jj < g * 16 + 16; jj += 2) {
+      a0 = fma(tile[r][jj], xq[jj], a0);
+      a1 = fma(tile[r][jj + 1], xq[jj + 1], a1);
+    }
+  }
+  part[g * kTsBS + r] = a0 + a1;
+  __syncthreads();
+  if (tid < kTsBS) {
+    const double sum = (part[tid] + part[kTsBS + tid]) + (part[2 * kTsBS + tid] + part[3 * kTsBS + tid]);
+    xq[tid] = tid < nr ? __ldcg(&X[r0 + tid]) - sum : 0.0;
+  }
+  __syncthreads();
+  // x_b = Dinv_b * rhs (column-major inverse)
+  double y0 = 0.0, y1 = 0.0;
+#pragma unroll
+  for (int j = g * 16; j < g * 16 + 16; j += 2) {
+    y0 = fma(dinv[r + kTsBS * j], xq[j], y0);
+    y1 = fma(dinv[r + kTsBS * (j + 1)], xq[j + 1], y1);
+  }
+  part[g * kTsBS + r] = y0 + y1;
+  __syncthreads();
+  if (tid < nr) {
+    X[r0 + tid] = (part[tid] + part[kTsBS + tid]) + (part[2 * kTsBS + tid] + part[3 * kTsBS + tid]);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    st_release_u32(&flags[b], 1u);
+  }
+}
+
+template <typename Ts>
+cudaError_t launch_trsv_inv(bool lower, int n, const Ts* T, int ldt, const double* Dinv, double* X,
+                            unsigned* flags, int* info, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int nblk = (n + kTsBS - 1) / kTsBS;
+  const size_t smem = sizeof(double) * ((size_t)kTsBS * (kTsBS + 1) + kTsBS * kTsBS + kTsBS + 4 * kTsBS);
+  cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(unsigned) * (size_t)(nblk + 1), s);
+  if (e != cudaSuccess) return e;
+  const uint64_t wait_ns = wait_timeout_ns();
+  if (lower) {
+    e = ensure_dyn_smem(trsv_inv_kernel<Ts, true>, smem);
+    if (e != cudaSuccess) return e;
+    trsv_inv_kernel<Ts, true><<<nblk, 256, smem, s>>>(n, T, ldt, Dinv, X, flags, info, wait_ns);
+  } else {
+    e = ensure_dyn_smem(trsv_inv_kernel<Ts, false>, smem);
+    if (e != cudaSuccess) return e;
+    trsv_inv_kernel<Ts, false><<<nblk, 256, smem, s>>>(n, T, ldt, Dinv, X, flags, info, wait_ns);
+  }
+  count_launch();
+  return cudaGetLastError();
+}
+template cudaError_t launch_trsv_inv<float>(bool, int, const float*, int, const double*, double*,
+                                            unsigned*, int*, cudaStream_t);
+template cudaError_t launch_trsv_inv<double>(bool, int, const double*, int, const double*, double*,
+                                             unsigned*, int*, cudaStream_t);
+
+}  // namespace gbla
