@@ -116,6 +116,29 @@ int gbla_lu_factor(int n, double *A, int lda, int *ipiv, int *d_info, int nb,
                    void *d_work, size_t work_bytes, gbla_stream_t stream);
 
 /*
+ * gbla_lu_factor without a workspace argument, for callers that cannot
+ * allocate device memory (for example code running inside a memory pool or a
+ * host application that owns every device allocation, or a path that must
+ * never reach the allocator). The paper has no counterpart; it computes the
+ * same factorisation, with the same kernels, as gbla_lu_factor.
+ *   Its only scratch, the panel kernel's exchange slots, is a fixed array of
+ *   about 290 KiB inside the library's device image (room for devices with up
+ *   to 256 multiprocessors; a device with more returns GBLA_ERR_WORKSPACE).
+ *   Every GPU that loads the library holds that array until the process
+ *   exits. The call itself allocates nothing.
+ *   The first call on a device looks up the array's device address for that
+ *   device (cudaGetSymbolAddress, with the device current); make that first
+ *   call before any stream capture.
+ *   All calls share the one array and it keeps the last call's contents
+ *   (each call clears it before use): calls whose work overlaps on the GPU --
+ *   on different streams, or from different host threads -- race with each
+ *   other and must be serialised by the caller.
+ * Arguments and d_info as for gbla_lu_factor.
+ */
+int gbla_lu_factor_static(int n, double *A, int lda, int *ipiv, int *d_info, int nb,
+                          gbla_stream_t stream);
+
+/*
  * Solve op(A) X = B from the gbla_lu_factor output (paper section 2, steps
  * a5-a6): trans = 0: apply P, L y = Pb (unit, forward), U x = y (back);
  * trans = 1: A^t x = b via U^t z = b, L^t w = z, x = P^t w.

@@ -44,6 +44,7 @@ _SIGS = {
     "gbla_get_wait_timeout_ns": ([], ctypes.c_uint64),
     "gbla_lu_factor_workspace": ([_i, _i], _sz),
     "gbla_lu_factor": ([_i, _vp, _i, _vp, _vp, _i, _vp, _sz, _vp], _i),
+    "gbla_lu_factor_static": ([_i, _vp, _i, _vp, _vp, _i, _vp], _i),
     "gbla_lu_solve_workspace": ([_i, _i], _sz),
     "gbla_lu_solve": ([_i, _i, _i, _vp, _i, _vp, _vp, _i, _vp, _vp, _sz, _vp], _i),
     "gbla_lu_factor_mixed_workspace": ([_i, _i, _i], _sz),

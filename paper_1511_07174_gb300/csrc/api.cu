@@ -153,17 +153,6 @@ static int ceil_div(int a, int b) { return (a + b - 1) / b; }
 // cooperative kernel, followed by the inner interchanges, substitution and
 // update restricted to the outer block. After the outer block: interchanges
 // on the rest of the matrix, the U row block, and the trailing update.
-struct LuWork {
-  double* slots;
-  unsigned* counters;
-  // mixed path only
-  void* Ak;
-  void* Bk;
-  int* eA;
-  int* eB;
-  int ldk;
-};
-
 static size_t lu_work_layout(Carver& c, int n, int nb, int prec, LuWork* w) {
   const int npanels = ceil_div(std::max(n, 1), kPanelWidth);
   double* slots = c.take<double>(panel_slots_doubles());
@@ -194,7 +183,7 @@ static size_t lu_work_layout(Carver& c, int n, int nb, int prec, LuWork* w) {
 }
 
 template <typename Ts>
-static cudaError_t blocked_lu(int n, Ts* A, int lda, int* ipiv, int* info, int nb, int prec,
+cudaError_t blocked_lu(int n, Ts* A, int lda, int* ipiv, int* info, int nb, int prec,
                               const LuWork& w, cudaStream_t s) {
   typedef Ts Tc_trsm;  // substitution arithmetic: FP64 for FP64 storage, FP32 for FP32
   cudaError_t e;
@@ -248,6 +237,11 @@ static cudaError_t blocked_lu(int n, Ts* A, int lda, int* ipiv, int* info, int n
   }
   return cudaSuccess;
 }
+
+template cudaError_t blocked_lu<double>(int, double*, int, int*, int*, int, int, const LuWork&,
+                                        cudaStream_t);
+template cudaError_t blocked_lu<float>(int, float*, int, int*, int*, int, int, const LuWork&,
+                                       cudaStream_t);
 
 static int check_nb(int nb) { return nb == 0 ? 256 : ((nb % 32 == 0 && nb >= 32 && nb <= 256) ? nb : -1); }
 

@@ -175,4 +175,19 @@ cudaError_t launch_mgs_step(int n, int j, double* V, int ldv, const double* w, d
 cudaError_t launch_gmres_update(int n, int k, const double* V, int ldv, const double* H, int ldh,
                                 const double* g, double* x, cudaStream_t s);
 
+// ---- blocked LU driver (api.cu) ---------------------------------------------
+struct LuWork {
+  double* slots;        // panel exchange slots, panel_slots_doubles(), zeroed per factorisation
+  unsigned* counters;
+  // mixed path only
+  void* Ak;
+  void* Bk;
+  int* eA;
+  int* eB;
+  int ldk;
+};
+template <typename Ts>
+cudaError_t blocked_lu(int n, Ts* A, int lda, int* ipiv, int* info, int nb, int prec,
+                       const LuWork& w, cudaStream_t s);
+
 }  // namespace gbla
