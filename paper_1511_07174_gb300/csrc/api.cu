@@ -154,12 +154,11 @@ static int ceil_div(int a, int b) { return (a + b - 1) / b; }
 // update restricted to the outer block. After the outer block: interchanges
 // on the rest of the matrix, the U row block, and the trailing update.
 static size_t lu_work_layout(Carver& c, int n, int nb, int prec, LuWork* w) {
-  const int npanels = ceil_div(std::max(n, 1), kPanelWidth);
   double* slots = c.take<double>(panel_slots_doubles());
-  unsigned* counters = c.take<unsigned>((size_t)npanels + 1);
+  int* plan = c.take<int>(laswp_plan_ints());
   if (w) {
     w->slots = slots;
-    w->counters = counters;
+    w->plan = plan;
     w->Ak = w->Bk = nullptr;
     w->eA = w->eB = nullptr;
     w->ldk = 0;
@@ -194,7 +193,7 @@ cudaError_t blocked_lu(int n, Ts* A, int lda, int* ipiv, int* info, int nb, int 
       PROF(KK_PANEL, s, launch_panel<Ts>(A + j0 + (size_t)j0 * lda, lda, n - j0, jb, j0, ipiv + j0, info,
                                          w.slots, (unsigned)(j0 / kPanelWidth), s));
       if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
-      PROF(KK_LASWP, s, launch_laswp<Ts>(A, lda, n, k0, j0, j0 + jb, k0 + kb, ipiv, j0, j0 + jb, s));
+      PROF(KK_LASWP, s, launch_laswp<Ts>(A, lda, n, k0, j0, j0 + jb, k0 + kb, ipiv, j0, j0 + jb, w.plan, s));
       if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
       const int nrest = k0 + kb - j0 - jb;
       if (nrest > 0) {
@@ -208,7 +207,7 @@ cudaError_t blocked_lu(int n, Ts* A, int lda, int* ipiv, int* info, int nb, int 
         if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
       }
     }
-    PROF(KK_LASWP, s, launch_laswp<Ts>(A, lda, n, 0, k0, k0 + kb, n, ipiv, k0, k0 + kb, s));
+    PROF(KK_LASWP, s, launch_laswp<Ts>(A, lda, n, 0, k0, k0 + kb, n, ipiv, k0, k0 + kb, w.plan, s));
     if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
     const int nt = n - k0 - kb;
     if (nt <= 0) continue;

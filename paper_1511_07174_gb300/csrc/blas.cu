@@ -12,47 +12,145 @@ namespace gbla {
 
 // ----------------------------------------------------------------------------
 // laswp: apply the interchanges ipiv[k1..k2) (1-based global rows, in order)
-// to the columns [c0, c1) and [c2, c3). One thread per column.
-template <typename T>
-__global__ void laswp_kernel(T* __restrict__ A, int lda, int nrows, int c0, int c1, int c2, int c3,
-                             const int* __restrict__ ipiv, int k1, int k2) {
-  __shared__ int sp[512];
+// to the columns [c0, c1) and [c2, c3), in two launches:
+//   plan  -- one warp replays the swaps on row labels (block rows in an array,
+//            rows below the block in a small open-addressing table) and writes
+//            the resulting list of (destination row, source row) moves;
+//   apply -- each warp moves its columns, all loads issued before any store.
+// Rows outside [k, nrows) named by a pivot are ignored.
+constexpr int kSwapMax = 256;   // interchanges per launch
+constexpr int kSwapHash = 1024;
+constexpr int kSwapColsPerCta = 32;
+
+size_t laswp_plan_ints() { return 1 + 4 * (size_t)kSwapMax; }
+
+__global__ void __launch_bounds__(32)
+    laswp_plan_kernel(const int* __restrict__ ipiv, int k1, int k2, int nrows, int* __restrict__ plan) {
+  __shared__ int blk[kSwapMax], piv[kSwapMax];
+  __shared__ int hk[kSwapHash], hv[kSwapHash];
+  __shared__ int slot_of[kSwapMax];
+  __shared__ int s_nout;
+  const int lane = threadIdx.x;
   const int nk = k2 - k1;
-  for (int i = threadIdx.x; i < nk; i += blockDim.x) sp[i] = ipiv[k1 + i] - 1;
+  for (int i = lane; i < nk; i += 32) {
+    blk[i] = k1 + i;
+    piv[i] = ipiv[k1 + i] - 1;
+  }
+  for (int i = lane; i < kSwapHash; i += 32) hk[i] = -1;
+  __syncwarp();
+  if (lane == 0) {
+    int nout = 0;
+    for (int k = k1; k < k2; ++k) {
+      const int p = piv[k - k1];
+      if (p <= k || p >= nrows) continue;
+      int* a = &blk[k - k1];
+      int* b;
+      if (p < k2) {
+        b = &blk[p - k1];
+      } else {
+        int h = (int)(((unsigned)p * 2654435761u) >> 22) & (kSwapHash - 1);
+        while (hk[h] != -1 && hk[h] != p) h = (h + 1) & (kSwapHash - 1);
+        if (hk[h] == -1) {
+          hk[h] = p;
+          hv[h] = p;
+          slot_of[nout++] = h;
+        }
+        b = &hv[h];
+      }
+      const int t = *a;
+      *a = *b;
+      *b = t;
+    }
+    s_nout = nout;
+  }
+  __syncwarp();
+  // compact the moves: block rows first (ascending), then the rows below
+  int* dst = plan + 1;
+  int* src = plan + 1 + 2 * kSwapMax;
+  int base = 0;
+  for (int i0 = 0; i0 < nk; i0 += 32) {
+    const int i = i0 + lane;
+    const bool mv = i < nk && blk[i] != k1 + i;
+    const unsigned m = __ballot_sync(0xffffffffu, mv);
+    if (mv) {
+      const int pos = base + __popc(m & ((1u << lane) - 1));
+      dst[pos] = k1 + i;
+      src[pos] = blk[i];
+    }
+    base += __popc(m);
+  }
+  const int nout = s_nout;
+  for (int i0 = 0; i0 < nout; i0 += 32) {
+    const int i = i0 + lane;
+    bool mv = false;
+    int h = 0;
+    if (i < nout) {
+      h = slot_of[i];
+      mv = hv[h] != hk[h];
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, mv);
+    if (mv) {
+      const int pos = base + __popc(m & ((1u << lane) - 1));
+      dst[pos] = hk[h];
+      src[pos] = hv[h];
+    }
+    base += __popc(m);
+  }
+  if (lane == 0) plan[0] = base;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+    laswp_apply_kernel(T* __restrict__ A, int lda, int c0, int c1, int c2, int c3,
+                       const int* __restrict__ plan) {
+  __shared__ int dst[2 * kSwapMax], src[2 * kSwapMax];
+  const int np = plan[0];
+  for (int i = threadIdx.x; i < np; i += blockDim.x) {
+    dst[i] = plan[1 + i];
+    src[i] = plan[1 + 2 * kSwapMax + i];
+  }
   __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int n1 = c1 - c0, n2 = c3 - c2;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n1 + n2) return;
-  const int col = t < n1 ? c0 + t : c2 + (t - n1);
-  T* a = A + (size_t)col * lda;
-  for (int i = 0; i < nk; ++i) {
-    const int k = k1 + i, p = sp[i];
-    if (p != k && p > k && p < nrows) {  // out-of-range pivots are ignored
-      T x = a[k];
-      a[k] = a[p];
-      a[p] = x;
+  constexpr int kPer = (2 * kSwapMax + 31) / 32;
+  for (int cc = warp; cc < kSwapColsPerCta; cc += (int)(blockDim.x >> 5)) {
+    const int t = blockIdx.x * kSwapColsPerCta + cc;
+    if (t >= n1 + n2) break;
+    const int col = t < n1 ? c0 + t : c2 + (t - n1);
+    T* a = A + (size_t)col * lda;
+    T v[kPer];
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int i = lane + 32 * q;
+      if (i < np) v[q] = a[src[i]];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int i = lane + 32 * q;
+      if (i < np) a[dst[i]] = v[q];
     }
   }
 }
 
 template <typename T>
 cudaError_t launch_laswp(T* A, int lda, int nrows, int c0, int c1, int c2, int c3, const int* ipiv,
-                         int k1, int k2, cudaStream_t s) {
+                         int k1, int k2, int* plan, cudaStream_t s) {
   if (c1 < c0) c1 = c0;
   if (c3 < c2) c3 = c2;
   const int ncols = (c1 - c0) + (c3 - c2);
   if (ncols <= 0 || k2 <= k1) return cudaSuccess;
-  if (k2 - k1 > 512) return cudaErrorInvalidValue;
-  const int threads = 128;
-  laswp_kernel<T><<<(ncols + threads - 1) / threads, threads, 0, s>>>(A, lda, nrows, c0, c1, c2, c3,
-                                                                     ipiv, k1, k2);
-  count_launch();
+  if (k2 - k1 > kSwapMax) return cudaErrorInvalidValue;
+  laswp_plan_kernel<<<1, 32, 0, s>>>(ipiv, k1, k2, nrows, plan);
+  laswp_apply_kernel<T><<<(ncols + kSwapColsPerCta - 1) / kSwapColsPerCta, 256, 0, s>>>(
+      A, lda, c0, c1, c2, c3, plan);
+  count_launch(2);
   return cudaGetLastError();
 }
 template cudaError_t launch_laswp<double>(double*, int, int, int, int, int, int, const int*, int,
-                                          int, cudaStream_t);
+                                          int, int*, cudaStream_t);
 template cudaError_t launch_laswp<float>(float*, int, int, int, int, int, int, const int*, int, int,
-                                         cudaStream_t);
+                                         int*, cudaStream_t);
 
 // ----------------------------------------------------------------------------
 // Low-precision conversion helpers (power-of-two sliver scaling).
@@ -124,9 +222,21 @@ __global__ void __launch_bounds__(256)
   }
   for (int i0 = 0; i0 < w; i0 += 32) {
     __syncthreads();
-    for (int idx = threadIdx.x; idx < 32 * w; idx += blockDim.x) {
-      const int cc = idx / w, r = idx - cc * w, i = i0 + cc;
-      Ls[idx] = (i < w && r > i) ? (Tc)L[r + (size_t)i * ldl] : (Tc)0;
+    {
+      // all loads of the chunk are issued before any shared-memory store
+      constexpr int kMaxPer = 32 * 256 / 256;
+      Ts v[kMaxPer];
+#pragma unroll
+      for (int t = 0; t < kMaxPer; ++t) {
+        const int idx = threadIdx.x + 256 * t;
+        const int cc = idx / w, r = idx - cc * w, i = i0 + cc;
+        v[t] = (idx < 32 * w && i < w && r > i) ? L[r + (size_t)i * ldl] : (Ts)0;
+      }
+#pragma unroll
+      for (int t = 0; t < kMaxPer; ++t) {
+        const int idx = threadIdx.x + 256 * t;
+        if (idx < 32 * w) Ls[idx] = (Tc)v[t];
+      }
     }
     __syncthreads();
     const int qi = i0 >> 5;
@@ -239,13 +349,20 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
   for (int i = 0; i < TM; ++i)
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc[i][j] = (T)0;
+  constexpr int PA = (BM * BK + NT - 1) / NT, PB = (BN * BK + NT - 1) / NT;
   for (int k0 = 0; k0 < K; k0 += BK) {
-    for (int idx = tid; idx < BM * BK; idx += NT) {
+    // all global loads of the tile pair are issued before any shared store
+    T va[PA], vb[PB];
+#pragma unroll
+    for (int t = 0; t < PA; ++t) {
+      const int idx = tid + NT * t;
       const int mm = idx % BM, kk = idx / BM;
       const int m = m0 + mm, k = k0 + kk;
-      As[kk][mm] = (m < M && k < K) ? A[m + (size_t)k * lda] : (T)0;
+      va[t] = (idx < BM * BK && m < M && k < K) ? A[m + (size_t)k * lda] : (T)0;
     }
-    for (int idx = tid; idx < BN * BK; idx += NT) {
+#pragma unroll
+    for (int t = 0; t < PB; ++t) {
+      const int idx = tid + NT * t;
       int nn, kk;
       if (TRANSB) {
         nn = idx % BN;
@@ -256,8 +373,22 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
       }
       const int nidx = n0 + nn, k = k0 + kk;
       T v = (T)0;
-      if (nidx < N && k < K) v = TRANSB ? B[nidx + (size_t)k * ldb] : B[k + (size_t)nidx * ldb];
-      Bs[kk][nn] = v;
+      if (idx < BN * BK && nidx < N && k < K)
+        v = TRANSB ? B[nidx + (size_t)k * ldb] : B[k + (size_t)nidx * ldb];
+      vb[t] = v;
+    }
+#pragma unroll
+    for (int t = 0; t < PA; ++t) {
+      const int idx = tid + NT * t;
+      if (idx < BM * BK) As[idx / BM][idx % BM] = va[t];
+    }
+#pragma unroll
+    for (int t = 0; t < PB; ++t) {
+      const int idx = tid + NT * t;
+      if (idx < BN * BK) {
+        if (TRANSB) Bs[idx / BN][idx % BN] = vb[t];
+        else Bs[idx % BK][idx / BK] = vb[t];
+      }
     }
     __syncthreads();
 #pragma unroll

@@ -263,17 +263,17 @@ template cudaError_t launch_diag_inv<double>(bool, bool, int, const double*, int
 size_t diag_inv_doubles(int n) { return (size_t)((n + kTsBS - 1) / kTsBS) * kTsBS * kTsBS; }
 
 // One right-hand side, forward (lower factor) or backward (upper factor).
-// Tiles of earlier blocks are prefetched into registers one step ahead so that
-// their loads overlap the wait for the previous block.
+// Thread (r, g) = (tid % 64, tid / 64) keeps, in registers, elements
+// (r, g + 4i), i < 16, of each 64 x 64 tile of its row block; the tile of the
+// next earlier block is loaded while the current one waits for its block's x.
 template <typename Ts, bool FWD>
 __global__ void __launch_bounds__(256)
     trsv_inv_kernel(int n, const Ts* __restrict__ T, int ldt, const double* __restrict__ Dinv,
                     double* X, unsigned* flags, int* info, uint64_t wait_ns) {
   extern __shared__ double smd[];
-  double (*tile)[kTsBS + 1] = reinterpret_cast<double (*)[kTsBS + 1]>(smd);      // 64 x 65
-  double* dinv = smd + kTsBS * (kTsBS + 1);                                       // 64 x 64
-  double* xq = dinv + kTsBS * kTsBS;                                              // 64
-  double* part = xq + kTsBS;                                                      // 4 x 64
+  double* dinv = smd;                  // 64 x 64, column-major
+  double* xq = dinv + kTsBS * kTsBS;   // 64
+  double* part = xq + kTsBS;           // 4 x 64
   __shared__ int s_t, s_abort;
   const int tid = threadIdx.x;
   const int nblk = (n + kTsBS - 1) / kTsBS;
@@ -293,31 +293,26 @@ __global__ void __launch_bounds__(256)
   const double* Db = Dinv + (size_t)b * kTsBS * kTsBS;
   for (int idx = tid; idx < kTsBS * kTsBS; idx += blockDim.x) dinv[idx] = Db[idx];
 
-  Ts pf[16];
-  auto prefetch = [&](int st) {
+  auto load = [&](int st, Ts (&v)[16]) {
     const int q = FWD ? st : nblk - 1 - st;
     const int c0 = q * kTsBS;
     const int nc = min(kTsBS, n - c0);
+    const Ts* base = T + (r0 + r) + (size_t)c0 * ldt;
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
-      const int idx = tid + 256 * i;
-      const int rr = idx & 63, jj = idx >> 6;
-      pf[i] = (rr < nr && jj < nc) ? T[(r0 + rr) + (size_t)(c0 + jj) * ldt] : (Ts)0;
+      const int jj = g + 4 * i;
+      v[i] = (r < nr && jj < nc) ? base[(size_t)jj * ldt] : (Ts)0;
     }
   };
   double a0 = 0.0, a1 = 0.0;
-  if (t_ord > 0) prefetch(0);
+  Ts cur[16];
+  if (t_ord > 0) load(0, cur);
   for (int st = 0; st < t_ord; ++st) {
     const int q = FWD ? st : nblk - 1 - st;
     const int c0 = q * kTsBS;
     const int nc = min(kTsBS, n - c0);
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const int idx = tid + 256 * i;
-      tile[idx & 63][idx >> 6] = (double)pf[i];
-    }
-    if (st + 1 < t_ord) prefetch(st + 1);
+    Ts nxt[16];
+    if (st + 1 < t_ord) load(st + 1, nxt);
     if (tid == 0) {
       if (!gbla_wait_geq(&flags[q], 1u, wait_ns)) {
         gbla_flag_timeout(info);
@@ -330,10 +325,15 @@ __global__ void __launch_bounds__(256)
     if (tid < kTsBS) xq[tid] = tid < nc ? __ldcg(&X[c0 + tid]) : 0.0;
     __syncthreads();
 #pragma unroll
-    for (int jj = g * 16; jj < g * 16 + 16; jj += 2) {
-      a0 = fma(tile[r][jj], xq[jj], a0);
-      a1 = fma(tile[r][jj + 1], xq[jj + 1], a1);
+    for (int i = 0; i < 16; i += 2) {
+      a0 = fma((double)cur[i], xq[g + 4 * i], a0);
+      a1 = fma((double)cur[i + 1], xq[g + 4 * (i + 1)], a1);
     }
+    if (st + 1 < t_ord) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) cur[i] = nxt[i];
+    }
+    __syncthreads();  // xq is rewritten next step
   }
   part[g * kTsBS + r] = a0 + a1;
   __syncthreads();
@@ -366,7 +366,7 @@ cudaError_t launch_trsv_inv(bool lower, int n, const Ts* T, int ldt, const doubl
                             unsigned* flags, int* info, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const int nblk = (n + kTsBS - 1) / kTsBS;
-  const size_t smem = sizeof(double) * ((size_t)kTsBS * (kTsBS + 1) + kTsBS * kTsBS + kTsBS + 4 * kTsBS);
+  const size_t smem = sizeof(double) * ((size_t)kTsBS * kTsBS + kTsBS + 4 * kTsBS);
   cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(unsigned) * (size_t)(nblk + 1), s);
   if (e != cudaSuccess) return e;
   const uint64_t wait_ns = wait_timeout_ns();
