@@ -151,6 +151,23 @@ int gbla_lu_solve(int trans, int n, int nrhs, const double *LU, int lda, const i
                   gbla_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * FP64 Cholesky A = L L^t of an SPD matrix (paper section 2; steps a1, a3,
+ * a4 for the SPD case). Lower triangle referenced and overwritten with L; the
+ * strict upper triangle is neither read nor written. Blocked right-looking
+ * with 64-column blocks: diagonal block in shared memory, the block column
+ * below it by substitution, the trailing lower triangle by a rank-64 update.
+ * No scratch. d_info: 0, or k > 0 when the leading minor of order k is not
+ * positive definite (the rest of the factor is then undefined).
+ * ------------------------------------------------------------------------ */
+int gbla_chol_factor(int n, double *A, int lda, int *d_info, gbla_stream_t stream);
+
+/* Solve A X = B from gbla_chol_factor: L y = b (forward), L^t x = y (back).
+ * B (n x nrhs, ldb) is overwritten by X. */
+size_t gbla_chol_solve_workspace(int n, int nrhs);
+int gbla_chol_solve(int n, int nrhs, const double *L, int lda, double *B, int ldb, int *d_info,
+                    void *d_work, size_t work_bytes, gbla_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Mixed-precision LU (steps a1-a4 in low precision). F (n x n FP32, ldf) is
  * set to fp32(A) and factored in place: panels in FP64 arithmetic rounded to
  * FP32, the U row block by FP32 substitution, the trailing update in the
@@ -197,6 +214,17 @@ int gbla_gmresir_solve(int n, const double *A, int lda, const float *F, int ldf,
                        const int *ipiv, const double *b, double *x,
                        const gbla_gmresir_opts *opts, gbla_gmresir_stats *stats,
                        void *d_work, size_t work_bytes, gbla_stream_t stream);
+
+/*
+ * Rank-k product C = alpha * U V^t + beta * C (FP64; U m x k, V n x k, C m x n;
+ * beta = 0 overwrites C without reading it). With alpha = -1, beta = 0,
+ * U = gb = A^{-t} g and V = x it forms the gradient of x = A^{-1} b with
+ * respect to A, gA = -gb x^t (step a10; the paper has no gradient -- this is
+ * the differentiation the solve is extended with).
+ */
+int gbla_rank_k_update(int m, int n, int k, double alpha, const double *U, int ldu,
+                       const double *V, int ldv, double beta, double *C, int ldc,
+                       gbla_stream_t stream);
 
 /*
  * Normwise backward error per column (step a7): d_beta[c] =

@@ -47,11 +47,15 @@ _SIGS = {
     "gbla_lu_factor_static": ([_i, _vp, _i, _vp, _vp, _i, _vp], _i),
     "gbla_lu_solve_workspace": ([_i, _i], _sz),
     "gbla_lu_solve": ([_i, _i, _i, _vp, _i, _vp, _vp, _i, _vp, _vp, _sz, _vp], _i),
+    "gbla_chol_factor": ([_i, _vp, _i, _vp, _vp], _i),
+    "gbla_chol_solve_workspace": ([_i, _i], _sz),
+    "gbla_chol_solve": ([_i, _i, _vp, _i, _vp, _i, _vp, _vp, _sz, _vp], _i),
     "gbla_lu_factor_mixed_workspace": ([_i, _i, _i], _sz),
     "gbla_lu_factor_mixed": ([_i, _vp, _i, _vp, _i, _vp, _vp, _i, _i, _vp, _sz, _vp], _i),
     "gbla_gmresir_workspace": ([_i, _i], _sz),
     "gbla_gmresir_solve": ([_i, _vp, _i, _vp, _i, _vp, _vp, _vp, ctypes.POINTER(GmresirOpts),
                             ctypes.POINTER(GmresirStats), _vp, _sz, _vp], _i),
+    "gbla_rank_k_update": ([_i, _i, _i, _d, _vp, _i, _vp, _i, _d, _vp, _i, _vp], _i),
     "gbla_backward_error_workspace": ([_i, _i], _sz),
     "gbla_backward_error": ([_i, _i, _vp, _i, _vp, _i, _vp, _i, _vp, _vp, _sz, _vp], _i),
 }

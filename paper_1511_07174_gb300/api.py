@@ -104,6 +104,35 @@ def lu_solve(LU, ipiv, B, trans=False, info=None):
     return X[:, 0] if vec else X
 
 
+# -------------------------------------------------------------------- Cholesky
+def chol_factor(A):
+    """A = L L^t (FP64, lower). Returns (matrix with L in its lower triangle, info device int32[1]).
+    The strict upper triangle is copied from A and left untouched."""
+    _require_cuda(A)
+    L = _lib.load()
+    n = A.shape[0]
+    F = colmajor(A, torch.float64, copy=True)
+    info = torch.zeros(1, dtype=torch.int32, device=A.device)
+    _check("gbla_chol_factor", L.gbla_chol_factor(n, _p(F), _ld(F), _p(info), _stream()))
+    return F, info
+
+
+def chol_solve(Lf, B, info=None):
+    """Solve A X = B from chol_factor's output. Returns X (column-major)."""
+    _require_cuda(Lf, B)
+    L = _lib.load()
+    n = Lf.shape[0]
+    vec = B.dim() == 1
+    X = colmajor(B, torch.float64, copy=True)
+    nrhs = X.shape[1]
+    info = torch.zeros(1, dtype=torch.int32, device=B.device) if info is None else info
+    Lc = colmajor(Lf, torch.float64)
+    ws = _ws(L.gbla_chol_solve_workspace(n, nrhs), B.device)
+    _check("gbla_chol_solve", L.gbla_chol_solve(n, nrhs, _p(Lc), _ld(Lc), _p(X), _ld(X), _p(info),
+                                                _p(ws), ws.numel(), _stream()))
+    return X[:, 0] if vec else X
+
+
 # ------------------------------------------------------------------ mixed path
 def lu_factor_mixed(A, prec="bf16", nb=256, F=None):
     """Low-precision LU of fp32(A): returns (F FP32 factors, ipiv, info)."""
@@ -168,6 +197,65 @@ def backward_error(A, X, B):
            L.gbla_backward_error(n, nrhs, _p(Ac), _ld(Ac), _p(Xc), _ld(Xc), _p(Bc), _ld(Bc), _p(beta),
                                  _p(ws), ws.numel(), _stream()))
     return beta[:nrhs]
+
+
+# ---------------------------------------------------------------------- autograd
+def rank_k_update(U, V, alpha=1.0, beta=0.0, C=None):
+    """C = alpha * U V^t + beta * C on the device (FP64). U: m x k, V: n x k."""
+    _require_cuda(U, V, C)
+    L = _lib.load()
+    Uc = colmajor(U, torch.float64)
+    Vc = colmajor(V, torch.float64)
+    m, k = Uc.shape
+    n = Vc.shape[0]
+    if C is None:
+        C = torch.empty_strided((m, n), (1, max(1, m)), dtype=torch.float64, device=U.device)
+        beta = 0.0
+    _check("gbla_rank_k_update",
+           L.gbla_rank_k_update(m, n, k, float(alpha), _p(Uc), _ld(Uc), _p(Vc), _ld(Vc), float(beta),
+                                _p(C), _ld(C), _stream()))
+    return C
+
+
+class _Solve(torch.autograd.Function):
+    """x = A^{-1} b with the LU (or Cholesky) factors kept for the backward pass:
+    gb = A^{-t} g by the transposed solves with the same factors, gA = -gb x^t."""
+
+    @staticmethod
+    def forward(ctx, A, b, method):
+        vec = b.dim() == 1
+        if method == "lu":
+            F, ipiv, info = lu_factor(A)
+            x = lu_solve(F, ipiv, b)
+        elif method == "chol":
+            F, info = chol_factor(A)
+            ipiv = None
+            x = chol_solve(F, b)
+        else:
+            raise ValueError(method)
+        ctx.method = method
+        ctx.vec = vec
+        ctx.save_for_backward(F, ipiv if ipiv is not None else torch.empty(0, device=A.device), x)
+        return x
+
+    @staticmethod
+    def backward(ctx, g):
+        F, ipiv, x = ctx.saved_tensors
+        g = g.contiguous()
+        if ctx.method == "lu":
+            gb = lu_solve(F, ipiv, g, trans=True)
+        else:
+            gb = chol_solve(F, g)
+        gb2 = gb.unsqueeze(1) if ctx.vec else gb
+        x2 = x.unsqueeze(1) if ctx.vec else x
+        gA = rank_k_update(gb2, x2, alpha=-1.0)
+        return gA, gb, None
+
+
+def solve(A, b, method="lu"):
+    """Differentiable solve of A x = b on the GPU (FP64). method: "lu" or "chol" (A SPD;
+    the gradient with respect to A is returned unsymmetrised, -gb x^t)."""
+    return _Solve.apply(A, b, method)
 
 
 # ------------------------------------------------------------- instrumentation

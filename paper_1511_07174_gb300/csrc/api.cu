@@ -434,6 +434,66 @@ int gbla_lu_solve(int trans, int n, int nrhs, const double* LU, int lda, const i
 }
 
 // ---------------------------------------------------------------------------
+int gbla_chol_factor(int n, double* A, int lda, int* d_info, gbla_stream_t stream) {
+  clear_error();
+  if (n < 0) return -1;
+  if (n > 0 && !A) return -2;
+  if (lda < std::max(1, n)) return -3;
+  if (!d_info) return -4;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  GBLA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), s));
+  if (n == 0) return GBLA_OK;
+  return cuda_status(launch_chol(n, A, lda, d_info, s));
+}
+
+size_t gbla_chol_solve_workspace(int n, int nrhs) {
+  if (n < 0 || nrhs < 0) return 0;
+  Carver c(nullptr, 0);
+  c.take<unsigned>(trsv_flags_count(std::max(n, 1)));
+  return c.off;
+}
+
+int gbla_chol_solve(int n, int nrhs, const double* L, int lda, double* B, int ldb, int* d_info,
+                    void* d_work, size_t work_bytes, gbla_stream_t stream) {
+  clear_error();
+  if (n < 0) return -1;
+  if (nrhs < 0) return -2;
+  if (n > 0 && !L) return -3;
+  if (lda < std::max(1, n)) return -4;
+  if (n > 0 && nrhs > 0 && !B) return -5;
+  if (ldb < std::max(1, n)) return -6;
+  if (!d_info) return -7;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!d_work || !aligned256(d_work)) return GBLA_ERR_WORKSPACE;
+  Carver c(d_work, work_bytes);
+  unsigned* flags = c.take<unsigned>(trsv_flags_count(std::max(n, 1)));
+  if (!c.ok) return GBLA_ERR_WORKSPACE;
+  GBLA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), s));
+  if (n == 0 || nrhs == 0) return GBLA_OK;
+  GBLA_TRYK(KK_TRSV, s, launch_trsv<double>(true, false, false, n, nrhs, L, lda, B, ldb, flags, d_info, s));
+  GBLA_TRYK(KK_TRSV, s, launch_trsv<double>(true, true, false, n, nrhs, L, lda, B, ldb, flags, d_info, s));
+  return GBLA_OK;
+}
+
+// ---------------------------------------------------------------------------
+int gbla_rank_k_update(int m, int n, int k, double alpha, const double* U, int ldu, const double* V,
+                       int ldv, double beta, double* C, int ldc, gbla_stream_t stream) {
+  clear_error();
+  if (m < 0) return -1;
+  if (n < 0) return -2;
+  if (k < 0) return -3;
+  if (m > 0 && k > 0 && !U) return -5;
+  if (ldu < std::max(1, m)) return -6;
+  if (n > 0 && k > 0 && !V) return -7;
+  if (ldv < std::max(1, n)) return -8;
+  if (m > 0 && n > 0 && !C) return -10;
+  if (ldc < std::max(1, m)) return -11;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  GBLA_TRYK(KK_UPDATE, s, launch_rank_k(m, n, k, alpha, U, ldu, V, ldv, beta, C, ldc, s));
+  return GBLA_OK;
+}
+
+// ---------------------------------------------------------------------------
 size_t gbla_backward_error_workspace(int n, int nrhs) {
   if (n < 0 || nrhs < 0) return 0;
   Carver c(nullptr, 0);

@@ -623,3 +623,59 @@ cudaError_t launch_permute_rows(int n, int nrhs, const int* perm, bool inverse, 
 }
 
 }  // namespace gbla
+
+namespace gbla {
+
+// ----------------------------------------------------------------------------
+// C (m x n) = alpha * U V^t + beta * C, U m x k, V n x k (k <= 16), FP64. The
+// gradient of a solve with respect to A (-gb x^t) is this product with
+// alpha = -1, beta = 0. Thread i of a CTA owns row i0 + i of 32 columns; the
+// k values of its row of U stay in registers and V's 32 rows sit in shared
+// memory, so every output element is written once, coalesced down a column.
+constexpr int kRkRows = 256, kRkCols = 32, kRkMaxK = 16;
+
+__global__ void __launch_bounds__(kRkRows)
+    rank_k_kernel(int m, int n, int k, double alpha, const double* __restrict__ U, int ldu,
+                  const double* __restrict__ V, int ldv, double beta, double* __restrict__ C,
+                  int ldc) {
+  __shared__ double vs[kRkCols][kRkMaxK];
+  const int i = blockIdx.x * kRkRows + threadIdx.x;
+  const int j0 = blockIdx.y * kRkCols;
+  for (int idx = threadIdx.x; idx < kRkCols * kRkMaxK; idx += blockDim.x) {
+    const int jj = idx % kRkCols, c = idx / kRkCols;
+    vs[jj][c] = (j0 + jj < n && c < k) ? V[(j0 + jj) + (size_t)c * ldv] : 0.0;
+  }
+  __syncthreads();
+  if (i >= m) return;
+  double u[kRkMaxK];
+#pragma unroll
+  for (int c = 0; c < kRkMaxK; ++c) u[c] = c < k ? U[i + (size_t)c * ldu] : 0.0;
+  const int jn = min(kRkCols, n - j0);
+  for (int jj = 0; jj < jn; ++jj) {
+    double acc = 0.0;
+#pragma unroll
+    for (int c = 0; c < kRkMaxK; ++c) acc = fma(u[c], vs[jj][c], acc);
+    double* cp = C + i + (size_t)(j0 + jj) * ldc;
+    *cp = beta == 0.0 ? alpha * acc : fma(alpha, acc, beta * *cp);
+  }
+}
+
+cudaError_t launch_rank_k(int m, int n, int k, double alpha, const double* U, int ldu,
+                          const double* V, int ldv, double beta, double* C, int ldc,
+                          cudaStream_t s) {
+  if (m <= 0 || n <= 0) return cudaSuccess;
+  for (int c0 = 0; c0 < k || (k == 0 && c0 == 0); c0 += kRkMaxK) {
+    const int kc = k - c0 < kRkMaxK ? k - c0 : kRkMaxK;
+    const double b = c0 == 0 ? beta : 1.0;
+    dim3 grid((m + kRkRows - 1) / kRkRows, (n + kRkCols - 1) / kRkCols);
+    rank_k_kernel<<<grid, kRkRows, 0, s>>>(m, n, kc, alpha, U + (size_t)c0 * ldu, ldu,
+                                           V + (size_t)c0 * ldv, ldv, b, C, ldc);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (k == 0) break;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace gbla

@@ -1,0 +1,136 @@
+// Cholesky factorisation A = L L^t of an SPD matrix (paper section 2), lower
+// triangle, blocked right-looking with 64-column blocks:
+//   potf2   -- the 64 x 64 diagonal block factored by one CTA in shared memory
+//              (column by column: d = a_jj, stop with info = j + 1 if d <= 0,
+//              l_jj = sqrt(d), l_ij = a_ij / l_jj, a_ik -= l_ij l_kj);
+//   trsm    -- the rows below it: L21 = A21 L11^{-t} in two 32-column halves
+//              (one thread per row, its 32 values in registers, the triangle
+//              in shared memory; the second half first receives the update
+//              from the first);
+//   update  -- A22 -= L21 L21^t on the lower triangle (the SIMT GEMM with its
+//              lower-triangle mask; tiles above the diagonal are skipped).
+// The strict upper triangle of A is never read or written.
+#include "common.cuh"
+#include "internal.h"
+
+namespace gbla {
+
+constexpr int kCholNb = 64;
+
+__global__ void __launch_bounds__(256)
+    potf2_kernel(int kb, double* __restrict__ A, int lda, int row0, int* __restrict__ info) {
+  __shared__ double D[kCholNb][kCholNb + 1];
+  __shared__ int s_bad;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < kCholNb * kCholNb; idx += blockDim.x) {
+    const int r = idx & 63, c = idx >> 6;
+    D[r][c] = (r < kb && c < kb && r >= c) ? A[r + (size_t)c * lda] : 0.0;
+  }
+  if (tid == 0) s_bad = 0;
+  __syncthreads();
+  // an earlier block that failed leaves the rest of the factor undefined; the
+  // first failure stays in info
+  for (int j = 0; j < kb; ++j) {
+    if (tid == 0) {
+      const double d = D[j][j];
+      if (!(d > 0.0)) {
+        s_bad = 1;
+        atomicCAS(info, 0, row0 + j + 1);
+      } else {
+        D[j][j] = sqrt(d);
+      }
+    }
+    __syncthreads();
+    if (s_bad) break;
+    const double rl = 1.0 / D[j][j];
+    for (int i = j + 1 + tid; i < kb; i += blockDim.x) D[i][j] *= rl;
+    __syncthreads();
+    // trailing part of the block: a_ik -= l_ij l_kj for i >= k > j
+    const int m = kb - j - 1;
+    for (int idx = tid; idx < m * m; idx += blockDim.x) {
+      const int i = j + 1 + idx % m, k = j + 1 + idx / m;
+      if (i >= k) D[i][k] = fma(-D[i][j], D[k][j], D[i][k]);
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < kCholNb * kCholNb; idx += blockDim.x) {
+    const int r = idx & 63, c = idx >> 6;
+    if (r < kb && c < kb && r >= c) A[r + (size_t)c * lda] = D[r][c];
+  }
+}
+
+// X L11^t = B for the M rows of B (M x kb, ldb); L11 kb x kb lower (kb <= 32),
+// one thread per row with its values in registers.
+constexpr int kCholTrsmW = 32;
+
+__global__ void __launch_bounds__(128)
+    chol_trsm_kernel(int M, int kb, const double* __restrict__ L, int lda, double* __restrict__ B,
+                     int ldb) {
+  __shared__ double Ls[kCholTrsmW][kCholTrsmW + 1];
+  __shared__ double rdiag[kCholTrsmW];
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < kCholTrsmW * kCholTrsmW; idx += blockDim.x) {
+    const int r = idx % kCholTrsmW, c = idx / kCholTrsmW;
+    Ls[r][c] = (r < kb && c < kb && r >= c) ? L[r + (size_t)c * lda] : (r == c ? 1.0 : 0.0);
+  }
+  __syncthreads();
+  if (tid < kCholTrsmW) rdiag[tid] = 1.0 / Ls[tid][tid];
+  __syncthreads();
+  const int row = blockIdx.x * blockDim.x + tid;
+  if (row >= M) return;
+  double x[kCholTrsmW];
+#pragma unroll
+  for (int k = 0; k < kCholTrsmW; ++k) x[k] = k < kb ? B[row + (size_t)k * ldb] : 0.0;
+#pragma unroll
+  for (int j = 0; j < kCholTrsmW; ++j) {
+    x[j] *= rdiag[j];
+#pragma unroll
+    for (int k = j + 1; k < kCholTrsmW; ++k) x[k] = fma(-x[j], Ls[k][j], x[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < kCholTrsmW; ++k)
+    if (k < kb) B[row + (size_t)k * ldb] = x[k];
+}
+
+cudaError_t launch_chol(int n, double* A, int lda, int* info, cudaStream_t s) {
+  for (int k0 = 0; k0 < n; k0 += kCholNb) {
+    const int kb = n - k0 < kCholNb ? n - k0 : kCholNb;
+    double* A11 = A + k0 + (size_t)k0 * lda;
+    prof_begin(KK_PANEL, s);
+    potf2_kernel<<<1, 256, 0, s>>>(kb, A11, lda, k0, info);
+    count_launch();
+    prof_end(KK_PANEL, s);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int m = n - k0 - kb;
+    if (m <= 0) break;
+    double* A21 = A11 + kb;
+    // L21 = A21 L11^{-t} in 32-column halves: solve the first half, update the
+    // second with it, solve the second half
+    for (int h0 = 0; h0 < kb; h0 += kCholTrsmW) {
+      const int hb = kb - h0 < kCholTrsmW ? kb - h0 : kCholTrsmW;
+      if (h0 > 0) {
+        prof_begin(KK_GEMM_SIMT, s);
+        e = launch_gemm_simt<double>(m, hb, h0, -1.0, A21, lda, A11 + h0, lda, true, 1.0,
+                                     A21 + (size_t)h0 * lda, lda, false, s);
+        prof_end(KK_GEMM_SIMT, s);
+        if (e != cudaSuccess) return e;
+      }
+      prof_begin(KK_TRSM, s);
+      chol_trsm_kernel<<<(m + 127) / 128, 128, 0, s>>>(m, hb, A11 + h0 + (size_t)h0 * lda, lda,
+                                                       A21 + (size_t)h0 * lda, lda);
+      count_launch();
+      prof_end(KK_TRSM, s);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+    prof_begin(KK_GEMM_SIMT, s);
+    e = launch_gemm_simt<double>(m, m, kb, -1.0, A21, lda, A21, lda, true, 1.0,
+                                 A21 + (size_t)kb * lda, lda, true, s);
+    prof_end(KK_GEMM_SIMT, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace gbla

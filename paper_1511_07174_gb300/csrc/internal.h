@@ -177,6 +177,14 @@ cudaError_t launch_mgs_step(int n, int j, double* V, int ldv, const double* w, d
 cudaError_t launch_gmres_update(int n, int k, const double* V, int ldv, const double* H, int ldh,
                                 const double* g, double* x, cudaStream_t s);
 
+// C = alpha * U V^t + beta * C (FP64; any k, in passes of 16)
+cudaError_t launch_rank_k(int m, int n, int k, double alpha, const double* U, int ldu,
+                          const double* V, int ldv, double beta, double* C, int ldc,
+                          cudaStream_t s);
+
+// ---- Cholesky (chol.cu) ------------------------------------------------------
+cudaError_t launch_chol(int n, double* A, int lda, int* info, cudaStream_t s);
+
 // ---- blocked LU driver (api.cu) ---------------------------------------------
 struct LuWork {
   double* slots;        // panel exchange slots, panel_slots_doubles(), zeroed per factorisation
