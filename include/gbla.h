@@ -77,7 +77,7 @@ const char *gbla_last_error(void);
  * gbla_prof_enable(mask): bracket every later launch group of the kinds set
  *   in mask (bit k = kind k) with a pair of CUDA events on its stream.
  *   Kinds: 0 panel, 1 laswp, 2 trsm, 3 gemm_simt, 4 gemm_tc, 5 convert,
- *   6 trsv, 7 matvec, 8 mgs, 9 gmres_update, 10 permute, 11 copy.
+ *   6 trsv, 7 matvec, 8 mgs, 9 gmres_update, 10 permute, 11 copy, 12 batched.
  * gbla_prof_read: number of recorded groups of `kind` and their summed
  *   device time in ms (waits for the events). gbla_prof_reset forgets them.
  */
@@ -214,6 +214,33 @@ int gbla_gmresir_solve(int n, const double *A, int lda, const float *F, int ldf,
                        const int *ipiv, const double *b, double *x,
                        const gbla_gmresir_opts *opts, gbla_gmresir_stats *stats,
                        void *d_work, size_t work_bytes, gbla_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Batched LU with partial pivoting + solve (step a9: the factorisation and
+ * the two substitutions of paper section 2 for every system of a batch), in
+ * ONE persistent kernel launch: a grid of SMs x ctas_per_sm CTAs pulls system
+ * indices from a counter (in d_order, or index order if d_order is NULL); one
+ * CTA factors and solves one whole system, in shared memory when it fits, in
+ * place in global memory otherwise. No host synchronisation and no
+ * allocation: the call can be captured in a CUDA graph.
+ * Device arrays of length batch: d_n (orders), d_A (column-major matrices,
+ * overwritten by their L\U), d_lda, d_ipiv (n_i ints each, 1-based),
+ * d_nrhs (0..4 right-hand sides each; NULL = factor only), d_B (n_i x nrhs_i,
+ * overwritten by X), d_ldb, d_info (first zero pivot per system or 0; may be
+ * NULL). max_n: an upper bound on the orders (sizes shared memory).
+ * threads (multiple of 32, 0 = 256) and ctas_per_sm (0 = 1) are tuning knobs.
+ * ------------------------------------------------------------------------ */
+size_t gbla_lu_batched_workspace(int batch);
+int gbla_lu_solve_batched(int batch, const int *d_n, double *const *d_A, const int *d_lda,
+                          int *const *d_ipiv, const int *d_nrhs, double *const *d_B,
+                          const int *d_ldb, int *d_info, const int *d_order, int max_n,
+                          int threads, int ctas_per_sm, void *d_work, size_t work_bytes,
+                          gbla_stream_t stream);
+int gbla_lu_solve_batched_f32(int batch, const int *d_n, float *const *d_A, const int *d_lda,
+                              int *const *d_ipiv, const int *d_nrhs, float *const *d_B,
+                              const int *d_ldb, int *d_info, const int *d_order, int max_n,
+                              int threads, int ctas_per_sm, void *d_work, size_t work_bytes,
+                              gbla_stream_t stream);
 
 /*
  * Rank-k product C = alpha * U V^t + beta * C (FP64; U m x k, V n x k, C m x n;

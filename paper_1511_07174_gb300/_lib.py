@@ -14,7 +14,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "gbla.h")
 GBLA_PREC = {"fp32": 1, "tf32": 2, "bf16": 3, "fp16": 4, "fp16x3": 5, "bf16x3": 6}
 GBLA_INFO_TIMEOUT = -1000
 KERNEL_KINDS = ["panel", "laswp", "trsm", "gemm_simt", "gemm_tc", "convert", "trsv", "matvec", "mgs",
-                "gmres_update", "permute", "copy"]
+                "gmres_update", "permute", "copy", "batched"]
 GBLA_ERR_NOT_CONVERGED = 1004
 
 _vp = ctypes.c_void_p
@@ -55,6 +55,9 @@ _SIGS = {
     "gbla_gmresir_workspace": ([_i, _i], _sz),
     "gbla_gmresir_solve": ([_i, _vp, _i, _vp, _i, _vp, _vp, _vp, ctypes.POINTER(GmresirOpts),
                             ctypes.POINTER(GmresirStats), _vp, _sz, _vp], _i),
+    "gbla_lu_batched_workspace": ([_i], _sz),
+    "gbla_lu_solve_batched": ([_i] + [_vp] * 9 + [_i, _i, _i, _vp, _sz, _vp], _i),
+    "gbla_lu_solve_batched_f32": ([_i] + [_vp] * 9 + [_i, _i, _i, _vp, _sz, _vp], _i),
     "gbla_rank_k_update": ([_i, _i, _i, _d, _vp, _i, _vp, _i, _d, _vp, _i, _vp], _i),
     "gbla_backward_error_workspace": ([_i, _i], _sz),
     "gbla_backward_error": ([_i, _i, _vp, _i, _vp, _i, _vp, _i, _vp, _vp, _sz, _vp], _i),

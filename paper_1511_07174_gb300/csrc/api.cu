@@ -269,8 +269,9 @@ const char* gbla_last_error(void) { return g_last_error; }
 
 uint64_t gbla_launch_count(void) { return g_launches.load(); }
 
-static const char* kKindNames[KK_COUNT] = {"panel", "laswp",  "trsm", "gemm_simt", "gemm_tc", "convert",
-                                           "trsv",  "matvec", "mgs",  "gmres_update", "permute", "copy"};
+static const char* kKindNames[KK_COUNT] = {"panel", "laswp",  "trsm", "gemm_simt",    "gemm_tc", "convert",
+                                           "trsv",  "matvec", "mgs",  "gmres_update", "permute", "copy",
+                                           "batched"};
 
 const char* gbla_kernel_kind_name(int kind) {
   return (kind >= 0 && kind < KK_COUNT) ? kKindNames[kind] : "";
@@ -473,6 +474,60 @@ int gbla_chol_solve(int n, int nrhs, const double* L, int lda, double* B, int ld
   GBLA_TRYK(KK_TRSV, s, launch_trsv<double>(true, false, false, n, nrhs, L, lda, B, ldb, flags, d_info, s));
   GBLA_TRYK(KK_TRSV, s, launch_trsv<double>(true, true, false, n, nrhs, L, lda, B, ldb, flags, d_info, s));
   return GBLA_OK;
+}
+
+// ---------------------------------------------------------------------------
+size_t gbla_lu_batched_workspace(int batch) {
+  if (batch < 0) return 0;
+  Carver c(nullptr, 0);
+  c.take<unsigned>(1);
+  return c.off;
+}
+
+}  // extern "C"
+
+template <typename T>
+static int lu_batched_entry(int batch, const int* d_n, T* const* d_A, const int* d_lda,
+                            int* const* d_ipiv, const int* d_nrhs, T* const* d_B, const int* d_ldb,
+                            int* d_info, const int* d_order, int max_n, int threads, int ctas_per_sm,
+                            void* d_work, size_t work_bytes, gbla_stream_t stream) {
+  clear_error();
+  if (batch < 0) return -1;
+  if (batch > 0 && !d_n) return -2;
+  if (batch > 0 && !d_A) return -3;
+  if (batch > 0 && !d_lda) return -4;
+  if (batch > 0 && !d_ipiv) return -5;
+  if (d_nrhs && (!d_B || !d_ldb)) return -7;
+  if (max_n < 0) return -11;
+  if (threads != 0 && (threads % 32 != 0 || threads < 32 || threads > 1024)) return -12;
+  if (ctas_per_sm < 0 || ctas_per_sm > 32) return -13;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!d_work || !aligned256(d_work)) return GBLA_ERR_WORKSPACE;
+  Carver c(d_work, work_bytes);
+  unsigned* counter = c.take<unsigned>(1);
+  if (!c.ok) return GBLA_ERR_WORKSPACE;
+  if (batch == 0) return GBLA_OK;
+  GBLA_TRYK(KK_BATCHED, s, launch_lu_batched<T>(batch, d_n, d_A, d_lda, d_ipiv, d_nrhs, d_B, d_ldb, d_info,
+                                              d_order, max_n, threads, ctas_per_sm, counter, s));
+  return GBLA_OK;
+}
+
+extern "C" {
+
+int gbla_lu_solve_batched(int batch, const int* d_n, double* const* d_A, const int* d_lda,
+                          int* const* d_ipiv, const int* d_nrhs, double* const* d_B, const int* d_ldb,
+                          int* d_info, const int* d_order, int max_n, int threads, int ctas_per_sm,
+                          void* d_work, size_t work_bytes, gbla_stream_t stream) {
+  return lu_batched_entry<double>(batch, d_n, d_A, d_lda, d_ipiv, d_nrhs, d_B, d_ldb, d_info, d_order,
+                                  max_n, threads, ctas_per_sm, d_work, work_bytes, stream);
+}
+
+int gbla_lu_solve_batched_f32(int batch, const int* d_n, float* const* d_A, const int* d_lda,
+                              int* const* d_ipiv, const int* d_nrhs, float* const* d_B,
+                              const int* d_ldb, int* d_info, const int* d_order, int max_n, int threads,
+                              int ctas_per_sm, void* d_work, size_t work_bytes, gbla_stream_t stream) {
+  return lu_batched_entry<float>(batch, d_n, d_A, d_lda, d_ipiv, d_nrhs, d_B, d_ldb, d_info, d_order,
+                                 max_n, threads, ctas_per_sm, d_work, work_bytes, stream);
 }
 
 // ---------------------------------------------------------------------------

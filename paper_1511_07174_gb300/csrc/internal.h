@@ -67,6 +67,7 @@ enum KernelKind {
   KK_UPDATE,
   KK_PERM,
   KK_COPY,
+  KK_BATCHED,
   KK_COUNT
 };
 void count_launch(int k = 1);                 // every kernel launch of the library
@@ -181,6 +182,13 @@ cudaError_t launch_gmres_update(int n, int k, const double* V, int ldv, const do
 cudaError_t launch_rank_k(int m, int n, int k, double alpha, const double* U, int ldu,
                           const double* V, int ldv, double beta, double* C, int ldc,
                           cudaStream_t s);
+
+// ---- batched LU + solve (batched.cu) -----------------------------------------
+template <typename T>
+cudaError_t launch_lu_batched(int batch, const int* n, T* const* A, const int* lda, int* const* ipiv,
+                              const int* nrhs, T* const* B, const int* ldb, int* info,
+                              const int* order, int max_n, int threads, int ctas_per_sm,
+                              unsigned* counter, cudaStream_t s);
 
 // ---- Cholesky (chol.cu) ------------------------------------------------------
 cudaError_t launch_chol(int n, double* A, int lda, int* info, cudaStream_t s);
