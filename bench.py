@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--nb", type=int, default=256)
     ap.add_argument("--restart", type=int, default=50)
     ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the other workloads (FP64 LU/Cholesky n=8192, batched, autograd)")
     ap.add_argument("--cpu-ksteps", type=int, default=8,
                     help="elimination steps of the oracle sample (bounded CPU baseline)")
     return ap.parse_args()
@@ -422,7 +424,140 @@ def run_ours(args, ws, rank):
                            for k, st, bo in zip(KAPPAS, last, betas_oracle)],
             "kernel_ms_first_warmup_step": {k: round(v[1], 3) for k, v in per_kind.items() if v[0]},
         }
+        if not args.no_secondary:
+            line["secondary"] = secondary(args, pk)
         print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------ secondary workloads
+def _event_ms(fn, reps=1):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def secondary(args, pk):
+    """The other measured workloads of the solver (one GPU): FP64 LU n = 512 and
+    n = 8192 (16 RHS, block size autotuned), FP64 Cholesky n = 8192, the batched
+    solver (4096 systems, FP64 and FP32, CUDA graph, autotuned launch shape) and
+    the differentiable solve at n = 4096 with 8 RHS."""
+    import oracle
+    from paper_1511_07174_gb300 import api, inputs
+    from paper_1511_07174_gb300.batched import BatchedLU
+    out = {}
+    dev = "cuda"
+    # FP64 reference rate: cuBLAS DGEMM (a denominator only, not on the solver path)
+    a = torch.randn(8192, 8192, dtype=torch.float64, device=dev)
+    torch.matmul(a, a)
+    ms = _event_ms(lambda: torch.matmul(a, a))
+    fp64_peak = 2 * 8192 ** 3 / (ms * 1e-3) / 1e12
+    del a
+    out["fp64_dgemm_tflops_measured"] = fp64_peak
+    # n = 512, one RHS, x_true = 1
+    n = 512
+    A = inputs.uniform(n, 0, dev)
+    b = A @ torch.ones(n, dtype=torch.float64, device=dev)
+    api.lu_solve(*api.lu_factor(A)[:2], b)
+    ms = _event_ms(lambda: api.lu_solve(*api.lu_factor(A)[:2], b), reps=5)
+    LU, piv, _ = api.lu_factor(A)
+    x = api.lu_solve(LU, piv, b)
+    An = np.asfortranarray(A.cpu().numpy())
+    LUo, ipo, _ = oracle.getrf(An)
+    out["lu_n512"] = {"ms": ms, "beta_oracle": float(oracle.backward_error(An, x.cpu().numpy(), b.cpu().numpy())[0]),
+                      "ipiv_equal_oracle": bool(np.array_equal(piv.cpu().numpy(), ipo))}
+    # n = 8192 FP64 LU, 16 RHS
+    n = 8192
+    A = inputs.uniform(n, 0, dev)
+    X_true = inputs.normal((n, 16), 1, dev)
+    B = A @ X_true
+    nb = api.tune_lu_nb(n)
+    LU, piv, info = api.lu_factor(A, nb=nb)
+    ms_f = _event_ms(lambda: api.lu_factor(A, nb=nb))
+    ms_s = _event_ms(lambda: api.lu_solve(LU, piv, B), reps=3)
+    X = api.lu_solve(LU, piv, B)
+    beta = float(api.backward_error(A, X, B).max().item())
+    tf = lu_flops(n) / (ms_f * 1e-3) / 1e12
+    out["lu_n8192_fp64"] = {"nb": nb, "factor_ms": ms_f, "tflops": tf, "frac_of_fp64_dgemm": tf / fp64_peak,
+                            "solve16_ms": ms_s,
+                            "solve_gbs": (n * n * 8) / (ms_s * 1e-3) / 1e9, "beta_max": beta}
+    del LU, X
+    # n = 8192 FP64 Cholesky
+    S = inputs.spd(n, 2, dev)
+    Xs = inputs.normal((n, 16), 3, dev)
+    Bs = S @ Xs
+    F, info = api.chol_factor(S)
+    ms_c = _event_ms(lambda: api.chol_factor(S))
+    Xc = api.chol_solve(F, Bs)
+    tfc = n ** 3 / 3.0 / (ms_c * 1e-3) / 1e12
+    out["chol_n8192_fp64"] = {"factor_ms": ms_c, "tflops": tfc, "frac_of_fp64_dgemm": tfc / fp64_peak,
+                              "beta_max": float(api.backward_error(S, Xc, Bs).max().item())}
+    del S, F, Xc, A, B
+    # batched: 4096 systems n_i in [16, 256], 1-4 RHS, one persistent launch in a CUDA graph
+    sizes, nrhs, As, Bs_, Xs_ = inputs.batched(4096, seed=7)
+    flops = sum(2.0 / 3.0 * m ** 3 + 2.0 * m * m * k for m, k in zip(sizes, nrhs))
+    for dt, name in ((torch.float64, "batched_fp64"), (torch.float32, "batched_fp32")):
+        bl = BatchedLU(As, Bs_, dtype=dt)
+        tune = bl.autotune()
+        bl.capture()
+        bl.replay()
+        ms_g = _event_ms(bl.replay, reps=3)           # restore copies + the solver launch
+        # the solver launch alone (eager, same launch shape), bracketed by events
+        bl.restore()
+        api.prof_enable(["batched"])
+        api.prof_reset()
+        bl.run()
+        torch.cuda.synchronize()
+        cnt, ms_k = api.prof_read("batched")
+        api.prof_enable([])
+        res, info = bl.results()
+        worst = 0.0
+        for (LU_, piv_, Xb), Ab, Bb in zip(res[:512], As[:512], Bs_[:512]):
+            Ad = np.asfortranarray(Ab.to(dt).to(torch.float64).numpy())
+            worst = max(worst, float(oracle.backward_error(Ad, Xb.to(torch.float64).numpy(),
+                                                           Bb.to(dt).to(torch.float64).numpy()).max()))
+        entry = {"systems": len(sizes), "graph_ms": ms_g, "kernel_ms": ms_k / max(cnt, 1),
+                 "systems_per_s": len(sizes) / (ms_k / max(cnt, 1) * 1e-3),
+                 "tflops": flops / (ms_k / max(cnt, 1) * 1e-3) / 1e12,
+                 "launch_shape": [bl.threads, bl.ctas_per_sm], "autotune_ms": tune.get("ms"),
+                 "beta_max_first512": worst}
+        if dt == torch.float64:
+            entry["frac_of_fp64_dgemm"] = entry["tflops"] / fp64_peak
+        out[name] = entry
+        del bl
+    # differentiable solve n = 4096, 8 RHS: forward and backward
+    A, b, g = inputs.autograd_problem(4096, 8, device=dev)
+    Ar = A.clone().requires_grad_(True)
+    br = b.clone().requires_grad_(True)
+    x = api.solve(Ar, br)
+    (x * g).sum().backward()
+    def fwd_bwd():
+        Ar.grad = None
+        br.grad = None
+        xx = api.solve(Ar, br)
+        (xx * g).sum().backward()
+    ms_fb = _event_ms(fwd_bwd)
+    Ar.grad = None
+    xx = api.solve(Ar, br)
+    loss = (xx * g).sum()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    loss.backward()
+    e1.record()
+    torch.cuda.synchronize()
+    ms_b = e0.elapsed_time(e1)
+    nbytes = 4096 * 4096 * 8 * 3    # gA written once + factors read by two triangular solves
+    out["autograd_n4096_8rhs"] = {"forward_backward_ms": ms_fb, "backward_ms": ms_b,
+                                  "backward_gbs": nbytes / (ms_b * 1e-3) / 1e9,
+                                  "backward_frac_of_hbm": nbytes / (ms_b * 1e-3) / 1e9 / pk.get("hbm_gbs", 6800.0)}
+    return out
 
 
 def main():

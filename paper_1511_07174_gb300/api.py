@@ -286,3 +286,32 @@ def prof_read(kind):
     _check("gbla_prof_read", _lib.load().gbla_prof_read(KERNEL_KINDS.index(kind), ctypes.byref(c),
                                                          ctypes.byref(t)))
     return c.value, t.value
+
+
+# ------------------------------------------------------------------ autotuning
+def tune_lu_nb(n, candidates=(64, 96, 128, 192, 256), device="cuda", use_cache=True, seed=0):
+    """Block size of the FP64 LU for order n, by timing each candidate on a
+    uniform random matrix of that order; remembered per GPU and n in the same
+    JSON cache as the batched launch shapes."""
+    from . import batched as _b
+    from . import inputs as _in
+    key = "lu_nb|%s|%d" % (torch.cuda.get_device_name(device), n)
+    cache = _b._load_cache() if use_cache else {}
+    if key in cache:
+        return cache[key]["nb"]
+    A = _in.uniform(n, seed, device)
+    res = {}
+    for nb in candidates:
+        lu_factor(A, nb=nb)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        lu_factor(A, nb=nb)
+        e1.record()
+        torch.cuda.synchronize()
+        res[nb] = e0.elapsed_time(e1)
+    best = min(res, key=res.get)
+    if use_cache:
+        cache[key] = {"nb": best, "candidates_ms": {str(k): v for k, v in res.items()}}
+        _b._store_cache(cache)
+    return best
