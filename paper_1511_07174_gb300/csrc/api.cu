@@ -190,10 +190,9 @@ cudaError_t blocked_lu(int n, Ts* A, int lda, int* ipiv, int* info, int nb, int 
     const int kb = std::min(nb, n - k0);
     for (int j0 = k0; j0 < k0 + kb; j0 += kPanelWidth) {
       const int jb = std::min(kPanelWidth, k0 + kb - j0);
+      // the panel launch also applies its interchanges to all other columns
       PROF(KK_PANEL, s, launch_panel<Ts>(A + j0 + (size_t)j0 * lda, lda, n - j0, jb, j0, ipiv + j0, info,
-                                         w.slots, (unsigned)(j0 / kPanelWidth), s));
-      if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
-      PROF(KK_LASWP, s, launch_laswp<Ts>(A, lda, n, k0, j0, j0 + jb, k0 + kb, ipiv, j0, j0 + jb, w.plan, s));
+                                         w.slots, (unsigned)(j0 / kPanelWidth), n, s));
       if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
       const int nrest = k0 + kb - j0 - jb;
       if (nrest > 0) {
@@ -207,8 +206,6 @@ cudaError_t blocked_lu(int n, Ts* A, int lda, int* ipiv, int* info, int nb, int 
         if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
       }
     }
-    PROF(KK_LASWP, s, launch_laswp<Ts>(A, lda, n, 0, k0, k0 + kb, n, ipiv, k0, k0 + kb, w.plan, s));
-    if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
     const int nt = n - k0 - kb;
     if (nt <= 0) continue;
     const bool tensor = prec_is_tensor(prec);

@@ -438,6 +438,12 @@ cudaError_t launch_gemm_simt(int M, int N, int K, T alpha, const T* A, int lda, 
       gemm_simt_kernel<T, BM, BN, BK, TM, TN, false, false><<<grid, 256, 0, s>>>(
           M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
     }
+  } else if (N <= 256 && !transB && !lower) {
+    // narrow updates (the inner steps of a block column): smaller tiles, more CTAs
+    constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4;
+    dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN);
+    gemm_simt_kernel<T, BM, BN, BK, TM, TN, false, false><<<grid, 256, 0, s>>>(
+        M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
   } else {
     constexpr int BM = 128, BN = 128, BK = 8, TM = 8, TN = 8;
     dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN);

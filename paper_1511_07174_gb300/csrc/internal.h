@@ -88,14 +88,17 @@ inline int prec_kmult(int p) { return prec_is_split(p) ? 3 : 1; }
 constexpr int kPanelWidth = 32;  // inner panel width handled by the cooperative kernel
 constexpr int kPanelSlotW = 72;  // doubles per published candidate slot
 
-// Exchange slots of the panel kernel: 2 * (num_sms + 1) slots. They must be
-// zeroed once before the first panel of a factorisation; panel_index (distinct
-// for every panel of one factorisation, < 2^25) tags the slot headers.
+// Exchange area of the panel kernel (slots for up to 256 SMs + pivot log).
+// It must be zeroed once before the first panel of a factorisation;
+// panel_index (distinct for every panel of one factorisation, < 2^25) tags the
+// words. A is the panel's top-left element (row = column = row0) of an
+// ncols-column matrix: besides factoring the panel, the launch applies the
+// panel's row interchanges to every other column of the matrix.
 size_t panel_slots_doubles();
 
 template <typename Ts>
 cudaError_t launch_panel(Ts* A, int lda, int m, int w, int row0, int* ipiv, int* info,
-                         double* slots, unsigned panel_index, cudaStream_t s);
+                         double* slots, unsigned panel_index, int ncols, cudaStream_t s);
 
 // Interchanges ipiv[k1..k2) (k2 - k1 <= 256) on columns [c0,c1) u [c2,c3);
 // rows outside [k, nrows) named by a pivot are ignored (defensive: never

@@ -20,11 +20,12 @@
 
 namespace gbla {
 
-// Room for the panel kernel's exchange slots on a device with up to
-// kStaticMaxSms multiprocessors (2 * (SMs + 1) slots of kPanelSlotW doubles),
-// followed by the interchange plan (kStaticPlanInts ints).
+// Room for the panel kernel's exchange area on a device with up to
+// kStaticMaxSms multiprocessors (2 * (SMs + 1) slots of kPanelSlotW doubles
+// and a pivot log of one word per panel column), followed by the interchange
+// plan (kStaticPlanInts ints).
 constexpr int kStaticMaxSms = 256;
-constexpr size_t kStaticSlotsDoubles = (size_t)2 * (kStaticMaxSms + 1) * kPanelSlotW;
+constexpr size_t kStaticSlotsDoubles = (size_t)2 * (kStaticMaxSms + 1) * kPanelSlotW + kPanelWidth;
 constexpr size_t kStaticPlanInts = 1 + 4 * 256;
 constexpr size_t kStaticTotalDoubles = kStaticSlotsDoubles + (kStaticPlanInts + 1) / 2;
 constexpr size_t kStaticSlotsBytes = kStaticTotalDoubles * sizeof(double);

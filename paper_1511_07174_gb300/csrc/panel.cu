@@ -36,10 +36,16 @@ constexpr int kSlotRow = 4;  // words before the row words in a slot (3 header w
 size_t panel_slots_doubles() {
   const DeviceProps& p = device_props();
   int c = p.num_sms > 0 ? p.num_sms : 160;
-  return (size_t)(2 * (c + 1)) * kPanelSlotW;
+  (void)c;
+  return (size_t)2 * (256 + 1) * kPanelSlotW + kPanelWidth;  // slots for <= 256 SMs + pivot log
 }
 
 typedef unsigned long long u64;
+
+// Word offset of the pivot log in the exchange area (after 2 * (kMaxSms + 1)
+// slots); the host sizes the area with the same bound.
+constexpr int kPanelMaxSms = 256;
+GBLA_DEVINL size_t panel_pivlog_offset() { return (size_t)2 * (kPanelMaxSms + 1) * kPanelSlotW; }
 
 GBLA_DEVINL void st_relaxed_u64(u64* p, u64 v) {
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
@@ -154,11 +160,50 @@ GBLA_DEVINL void warp_merge(PivKey<Ts>& p) {
   for (int o = 16; o > 0; o >>= 1) p.shfl_merge(o);
 }
 
+// Interchange role of the panel launch: the last S CTAs apply each column's
+// row interchange (rows j0 + j and j0 + p) to every column of the matrix
+// outside the panel, as soon as CTA 0 has logged the pivot of column j. They
+// only read the exchange (never publish), so they cannot slow the panel down;
+// each thread always owns the same columns, so program order keeps the
+// interchanges of one column in sequence.
+template <typename Ts>
+GBLA_DEVINL void swapper_role(Ts* __restrict__ Aall, int lda, int ncols, int j0, int w, int jend,
+                              int sidx, int S, const u64* __restrict__ pivlog, unsigned tag_base,
+                              int* __restrict__ info, uint64_t wait_ns) {
+  __shared__ int s_sp, s_sabort;
+  const int other = ncols - w;
+  const int per = (other + S - 1) / S;
+  const int cbeg = sidx * per, cend = min(other, cbeg + per);
+  for (int j = 0; j < jend; ++j) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const u64 tag = (u64)(tag_base | (unsigned)(j + 1)) << 32;
+      uint32_t pl[1] = {0};
+      s_sabort = ll_read<1>(pivlog + j, tag, wait_ns, pl) ? 0 : 1;
+      s_sp = (int)pl[0];
+    }
+    __syncthreads();
+    if (s_sabort) {
+      if (threadIdx.x == 0) gbla_flag_timeout(info);
+      return;
+    }
+    const int p = s_sp;
+    if (p == j) continue;
+    for (int q = cbeg + (int)threadIdx.x; q < cend; q += blockDim.x) {
+      const int col = q < j0 ? q : q + w;
+      Ts* a = Aall + (size_t)col * lda;
+      const Ts x = a[j0 + j];
+      a[j0 + j] = a[j0 + p];
+      a[j0 + p] = x;
+    }
+  }
+}
+
 template <typename Ts>
 __global__ void __launch_bounds__(kPanelThreads)
     panel_kernel(Ts* __restrict__ A, int lda, int m, int w, int row0, int R,
                  int* __restrict__ ipiv, int* __restrict__ info, double* __restrict__ slots_d,
-                 unsigned tag_base, uint64_t wait_ns) {
+                 unsigned tag_base, uint64_t wait_ns, int ncols, int S) {
   typedef PivKey<Ts> Key;
   constexpr int KW = Key::kWords;
   extern __shared__ double smem[];
@@ -171,7 +216,14 @@ __global__ void __launch_bounds__(kPanelThreads)
   __shared__ int s_abort;
 
   u64* slots = reinterpret_cast<u64*>(slots_d);
-  const int C = gridDim.x;
+  const int C = gridDim.x - S;  // panel CTAs; the last S CTAs apply the interchanges
+  if ((int)blockIdx.x >= C) {
+    swapper_role<Ts>(A - (size_t)row0 - (size_t)row0 * lda, lda, ncols, row0, w, min(w, m),
+                     (int)blockIdx.x - C, S,
+                     reinterpret_cast<const u64*>(slots_d) + panel_pivlog_offset(), tag_base, info,
+                     wait_ns);
+    return;
+  }
   const int c = blockIdx.x;
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
@@ -280,6 +332,8 @@ __global__ void __launch_bounds__(kPanelThreads)
     }
     if (c == 0 && tid == 0) {
       ipiv[j] = row0 + p + 1;
+      if (S > 0)
+        st_relaxed_u64(slots + panel_pivlog_offset() + j, tag | (u64)(unsigned)p);
       if (gk.zero_pivot()) atomicCAS(info, 0, row0 + j + 1);
     }
     __syncthreads();
@@ -327,7 +381,7 @@ template <typename Ts, int RPT>
 __global__ void __launch_bounds__(kPanelThreads, 1)
     panel_reg_kernel(Ts* __restrict__ A, int lda, int m, int w, int row0, int R,
                      int* __restrict__ ipiv, int* __restrict__ info, double* __restrict__ slots_d,
-                     unsigned tag_base, uint64_t wait_ns) {
+                     unsigned tag_base, uint64_t wait_ns, int ncols, int S) {
   typedef PivKey<Ts> Key;
   constexpr int KW = Key::kWords;
   constexpr int W = kPanelWidth;
@@ -338,7 +392,14 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
   __shared__ int s_abort;
 
   u64* slots = reinterpret_cast<u64*>(slots_d);
-  const int C = gridDim.x;
+  const int C = gridDim.x - S;  // panel CTAs; the last S CTAs apply the interchanges
+  if ((int)blockIdx.x >= C) {
+    swapper_role<Ts>(A - (size_t)row0 - (size_t)row0 * lda, lda, ncols, row0, w, min(w, m),
+                     (int)blockIdx.x - C, S,
+                     reinterpret_cast<const u64*>(slots_d) + panel_pivlog_offset(), tag_base, info,
+                     wait_ns);
+    return;
+  }
   const int c = blockIdx.x;
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
@@ -465,6 +526,8 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
       }
       if (c == 0 && tid == 0) {
         ipiv[j] = row0 + p + 1;
+      if (S > 0)
+        st_relaxed_u64(slots + panel_pivlog_offset() + j, tag | (u64)(unsigned)p);
         if (gk.zero_pivot()) atomicCAS(info, 0, row0 + j + 1);
       }
       if (tid >= kPanelWidth * 2 && tid < kPanelWidth * 2 + kPanelWidth)  // pad columns >= w
@@ -514,7 +577,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
 
 template <typename Ts>
 cudaError_t launch_panel(Ts* A, int lda, int m, int w, int row0, int* ipiv, int* info,
-                         double* slots, unsigned panel_index, cudaStream_t s) {
+                         double* slots, unsigned panel_index, int ncols, cudaStream_t s) {
   if (m <= 0 || w <= 0) return cudaSuccess;
   if (w > kPanelWidth) return cudaErrorInvalidValue;
   const DeviceProps& dp = device_props();
@@ -535,28 +598,38 @@ cudaError_t launch_panel(Ts* A, int lda, int m, int w, int row0, int* ipiv, int*
     R = (m + C - 1) / C;
   }
   C = (m + R - 1) / R;
+  // interchange CTAs: enough that each owns ~512 of the other columns, while
+  // the whole grid stays co-resident (one CTA per SM)
+  int S = 0;
+  if (ncols > w) {
+    S = (ncols - w + 511) / 512;
+    if (S > 32) S = 32;
+    if (S > dp.num_sms - C) S = dp.num_sms - C;
+    if (S < 1) S = 0;  // no room: caller must apply the interchanges itself
+  }
+  if (S == 0 && ncols > w) return cudaErrorInvalidConfiguration;
   uint64_t wait_ns = wait_timeout_ns();
   unsigned tag_base = (panel_index + 1u) << 6;
-  void* args[] = {&A, &lda, &m, &w, &row0, &R, &ipiv, &info, &slots, &tag_base, &wait_ns};
+  void* args[] = {&A, &lda, &m, &w, &row0, &R, &ipiv, &info, &slots, &tag_base, &wait_ns, &ncols, &S};
   count_launch();
   if (R <= kPanelThreads)
-    return cudaLaunchCooperativeKernel((const void*)panel_reg_kernel<Ts, 1>, dim3(C),
+    return cudaLaunchCooperativeKernel((const void*)panel_reg_kernel<Ts, 1>, dim3(C + S),
                                        dim3(kPanelThreads), args, 0, s);
   if (R <= 2 * kPanelThreads)
-    return cudaLaunchCooperativeKernel((const void*)panel_reg_kernel<Ts, 2>, dim3(C),
+    return cudaLaunchCooperativeKernel((const void*)panel_reg_kernel<Ts, 2>, dim3(C + S),
                                        dim3(kPanelThreads), args, 0, s);
   // very tall panels: shared-memory slab
   size_t smem = ((size_t)w * R + 2 * kPanelWidth) * sizeof(Ts) + 16;
   if (smem > dp.smem_optin) return cudaErrorInvalidValue;
   cudaError_t ea = ensure_dyn_smem(panel_kernel<Ts>, smem);
   if (ea != cudaSuccess) return ea;
-  return cudaLaunchCooperativeKernel((const void*)panel_kernel<Ts>, dim3(C), dim3(kPanelThreads),
+  return cudaLaunchCooperativeKernel((const void*)panel_kernel<Ts>, dim3(C + S), dim3(kPanelThreads),
                                      args, smem, s);
 }
 
 template cudaError_t launch_panel<double>(double*, int, int, int, int, int*, int*, double*,
-                                          unsigned, cudaStream_t);
+                                          unsigned, int, cudaStream_t);
 template cudaError_t launch_panel<float>(float*, int, int, int, int, int*, int*, double*,
-                                         unsigned, cudaStream_t);
+                                         unsigned, int, cudaStream_t);
 
 }  // namespace gbla
