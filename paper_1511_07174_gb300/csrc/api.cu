@@ -598,6 +598,8 @@ struct IrWork {
   double* slots;
   unsigned* counter;
   unsigned* flags;
+  double* t1;
+  double* t2;
   double* DinvL;
   double* DinvU;
   int* info;
@@ -623,6 +625,8 @@ static size_t ir_layout(Carver& c, int n, int m, IrWork* w) {
   t.slots = c.take<double>(mgs_slots_doubles());
   t.counter = c.take<unsigned>(1);
   t.flags = c.take<unsigned>(trsv_flags_count(nn));
+  t.t1 = c.take<double>(nn);
+  t.t2 = c.take<double>(nn);
   t.DinvL = c.take<double>(diag_inv_doubles(nn));
   t.DinvU = c.take<double>(diag_inv_doubles(nn));
   t.info = c.take<int>(1);
@@ -640,16 +644,17 @@ size_t gbla_gmresir_workspace(int n, int restart_m) {
 }
 
 // dst <- M^{-1} src with M = P^t L U (FP32 factors, FP64 arithmetic, inverted
-// 64 x 64 diagonal blocks of L and U formed once per solve call)
+// 64 x 64 diagonal blocks of L and U formed once per solve call); t1, t2:
+// n-double temporaries; src and dst distinct
 static cudaError_t apply_minv(int n, const float* F, int ldf, const int* perm, const double* DinvL,
-                              const double* DinvU, const double* src, double* dst, unsigned* flags,
-                              int* info, cudaStream_t s) {
+                              const double* DinvU, const double* src, double* dst, double* t1,
+                              double* t2, unsigned* flags, int* info, cudaStream_t s) {
   cudaError_t e;
-  PROF(KK_PERM, s, launch_permute_rows(n, 1, perm, false, src, n, dst, n, s));
+  PROF(KK_PERM, s, launch_permute_rows(n, 1, perm, false, src, n, t1, n, s));
   if (e != cudaSuccess) return e;
-  PROF(KK_TRSV, s, launch_trsv_inv<float>(true, n, F, ldf, DinvL, dst, flags, info, s));
+  PROF(KK_TRSV, s, launch_trsv_inv<float>(true, n, F, ldf, DinvL, t1, t2, flags, info, s));
   if (e != cudaSuccess) return e;
-  PROF(KK_TRSV, s, launch_trsv_inv<float>(false, n, F, ldf, DinvU, dst, flags, info, s));
+  PROF(KK_TRSV, s, launch_trsv_inv<float>(false, n, F, ldf, DinvU, t2, dst, flags, info, s));
   return e;
 }
 
@@ -699,7 +704,7 @@ int gbla_gmresir_solve(int n, const double* A, int lda, const float* F, int ldf,
   GBLA_TRYK(KK_TRSV, s, launch_diag_inv<float>(true, true, n, F, ldf, w.DinvL, s));
   GBLA_TRYK(KK_TRSV, s, launch_diag_inv<float>(false, false, n, F, ldf, w.DinvU, s));
   GBLA_TRYK(KK_MATVEC, s, launch_row_abs_sum_max(n, A, lda, w.part, w.anorm, s));
-  GBLA_TRY(apply_minv(n, F, ldf, w.perm, w.DinvL, w.DinvU, b, x, w.flags, w.info, s));
+  GBLA_TRY(apply_minv(n, F, ldf, w.perm, w.DinvL, w.DinvU, b, x, w.t1, w.t2, w.flags, w.info, s));
   int rc = GBLA_OK;
   for (int outer = 0;; ++outer) {
     GBLA_TRYK(KK_MATVEC, s, launch_residual(n, 1, A, lda, x, n, b, n, w.r, n, w.part, s));
@@ -716,7 +721,7 @@ int gbla_gmresir_solve(int n, const double* A, int lda, const float* F, int ldf,
     }
     if (outer >= opts->max_outer) return GBLA_ERR_NOT_CONVERGED;
     // z = M^{-1} r, v_0 = z / ||z||
-    GBLA_TRY(apply_minv(n, F, ldf, w.perm, w.DinvL, w.DinvU, w.r, w.w, w.flags, w.info, s));
+    GBLA_TRY(apply_minv(n, F, ldf, w.perm, w.DinvL, w.DinvU, w.r, w.w, w.t1, w.t2, w.flags, w.info, s));
     GBLA_TRYK(KK_MGS, s, launch_mgs_step(n, -1, w.V, w.ldv, w.w, w.H, m + 1, w.cs, w.sn, w.g, w.st, w.slots,
                              w.counter, w.info, s));
     double beta_in = 0.0;
@@ -730,7 +735,7 @@ int gbla_gmresir_solve(int n, const double* A, int lda, const float* F, int ldf,
     for (int j = 0; j < m; ++j) {
       // w = M^{-1} A v_j
       GBLA_TRYK(KK_MATVEC, s, launch_residual(n, 1, A, lda, w.V + (size_t)j * w.ldv, n, nullptr, n, w.w, n, w.part, s));
-      GBLA_TRY(apply_minv(n, F, ldf, w.perm, w.DinvL, w.DinvU, w.w, w.r, w.flags, w.info, s));
+      GBLA_TRY(apply_minv(n, F, ldf, w.perm, w.DinvL, w.DinvU, w.w, w.r, w.t1, w.t2, w.flags, w.info, s));
       GBLA_TRYK(KK_MGS, s, launch_mgs_step(n, j, w.V, w.ldv, w.r, w.H, m + 1, w.cs, w.sn, w.g, w.st, w.slots,
                                w.counter, w.info, s));
       double res = 0.0;

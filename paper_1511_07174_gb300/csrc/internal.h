@@ -150,9 +150,11 @@ size_t diag_inv_doubles(int n);
 template <typename Ts>
 cudaError_t launch_diag_inv(bool lower, bool unit, int n, const Ts* T, int ldt, double* Dinv,
                             cudaStream_t s);
+// X <- T^{-1} rhs (X and rhs distinct; X is overwritten, flags: one uint).
 template <typename Ts>
-cudaError_t launch_trsv_inv(bool lower, int n, const Ts* T, int ldt, const double* Dinv, double* X,
-                            unsigned* flags, int* info, cudaStream_t s);
+cudaError_t launch_trsv_inv(bool lower, int n, const Ts* T, int ldt, const double* Dinv,
+                            const double* rhs, double* X, unsigned* flags, int* info,
+                            cudaStream_t s);
 
 cudaError_t launch_ipiv_to_perm(int n, const int* ipiv, int* perm, cudaStream_t s);
 // dst[i, c] = src[perm[i], c] (forward) or dst[perm[i], c] = src[i, c] (inverse)

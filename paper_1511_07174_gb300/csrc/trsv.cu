@@ -263,22 +263,30 @@ template cudaError_t launch_diag_inv<double>(bool, bool, int, const double*, int
 size_t diag_inv_doubles(int n) { return (size_t)((n + kTsBS - 1) / kTsBS) * kTsBS * kTsBS; }
 
 // One right-hand side, forward (lower factor) or backward (upper factor).
+// The solution goes to X, which the launcher first fills with an all-ones bit
+// pattern (a NaN that arithmetic does not produce): a block's x values
+// announce themselves, so a consumer polls the 64 values it needs instead of a
+// flag followed by a second load, and the producer needs no fence.
 // Thread (r, g) = (tid % 64, tid / 64) keeps, in registers, elements
 // (r, g + 4i), i < 16, of each 64 x 64 tile of its row block; the tile of the
-// next earlier block is loaded while the current one waits for its block's x.
+// next earlier block is loaded while the current one waits for its x.
+constexpr unsigned long long kXUnset = 0xffffffffffffffffull;
+
 template <typename Ts, bool FWD>
 __global__ void __launch_bounds__(256)
     trsv_inv_kernel(int n, const Ts* __restrict__ T, int ldt, const double* __restrict__ Dinv,
-                    double* X, unsigned* flags, int* info, uint64_t wait_ns) {
+                    const double* __restrict__ rhs, double* X, unsigned* ticket, int* info,
+                    uint64_t wait_ns) {
   extern __shared__ double smd[];
   double* dinv = smd;                  // 64 x 64, column-major
   double* xq = dinv + kTsBS * kTsBS;   // 64
   double* part = xq + kTsBS;           // 4 x 64
+  double* rb = part + 4 * kTsBS;       // 64: this block's right-hand side
   __shared__ int s_t, s_abort;
   const int tid = threadIdx.x;
   const int nblk = (n + kTsBS - 1) / kTsBS;
   if (tid == 0) {
-    s_t = (int)atomicAdd(&flags[nblk], 1u);
+    s_t = (int)atomicAdd(ticket, 1u);
     s_abort = 0;
   }
   __syncthreads();
@@ -289,9 +297,10 @@ __global__ void __launch_bounds__(256)
   const int nr = min(kTsBS, n - r0);
   const int r = tid & 63, g = tid >> 6;
 
-  // the inverse of the diagonal block, needed last, is staged first
+  // the inverse of the diagonal block and the right-hand side, needed last, are staged first
   const double* Db = Dinv + (size_t)b * kTsBS * kTsBS;
   for (int idx = tid; idx < kTsBS * kTsBS; idx += blockDim.x) dinv[idx] = Db[idx];
+  if (tid < kTsBS) rb[tid] = tid < nr ? rhs[r0 + tid] : 0.0;
 
   auto load = [&](int st, Ts (&v)[16]) {
     const int q = FWD ? st : nblk - 1 - st;
@@ -313,17 +322,31 @@ __global__ void __launch_bounds__(256)
     const int nc = min(kTsBS, n - c0);
     Ts nxt[16];
     if (st + 1 < t_ord) load(st + 1, nxt);
-    if (tid == 0) {
-      if (!gbla_wait_geq(&flags[q], 1u, wait_ns)) {
-        gbla_flag_timeout(info);
-        s_abort = 1;
+    if (tid < kTsBS) {
+      double v = 0.0;
+      if (tid < nc) {
+        const unsigned long long* px = reinterpret_cast<const unsigned long long*>(X + c0 + tid);
+        unsigned long long bits;
+        asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(bits) : "l"(px) : "memory");
+        if (bits == kXUnset) {
+          const uint64_t t0 = gbla_now_ns();
+          do {
+            asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(bits) : "l"(px) : "memory");
+            if (gbla_now_ns() - t0 > wait_ns) {
+              s_abort = 1;
+              break;
+            }
+          } while (bits == kXUnset);
+        }
+        v = __longlong_as_double((long long)bits);
       }
-      __threadfence();
+      xq[tid] = v;
     }
     __syncthreads();
-    if (s_abort) return;
-    if (tid < kTsBS) xq[tid] = tid < nc ? __ldcg(&X[c0 + tid]) : 0.0;
-    __syncthreads();
+    if (s_abort) {
+      if (tid == 0) gbla_flag_timeout(info);
+      return;
+    }
 #pragma unroll
     for (int i = 0; i < 16; i += 2) {
       a0 = fma((double)cur[i], xq[g + 4 * i], a0);
@@ -339,7 +362,7 @@ __global__ void __launch_bounds__(256)
   __syncthreads();
   if (tid < kTsBS) {
     const double sum = (part[tid] + part[kTsBS + tid]) + (part[2 * kTsBS + tid] + part[3 * kTsBS + tid]);
-    xq[tid] = tid < nr ? __ldcg(&X[r0 + tid]) - sum : 0.0;
+    xq[tid] = tid < nr ? rb[tid] - sum : 0.0;
   }
   __syncthreads();
   // x_b = Dinv_b * rhs (column-major inverse)
@@ -352,39 +375,39 @@ __global__ void __launch_bounds__(256)
   part[g * kTsBS + r] = y0 + y1;
   __syncthreads();
   if (tid < nr) {
-    X[r0 + tid] = (part[tid] + part[kTsBS + tid]) + (part[2 * kTsBS + tid] + part[3 * kTsBS + tid]);
-  }
-  __syncthreads();
-  if (tid == 0) {
-    __threadfence();
-    st_release_u32(&flags[b], 1u);
+    const double xv = (part[tid] + part[kTsBS + tid]) + (part[2 * kTsBS + tid] + part[3 * kTsBS + tid]);
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(xv);
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(X + r0 + tid), "l"(bits) : "memory");
   }
 }
 
 template <typename Ts>
-cudaError_t launch_trsv_inv(bool lower, int n, const Ts* T, int ldt, const double* Dinv, double* X,
-                            unsigned* flags, int* info, cudaStream_t s) {
+cudaError_t launch_trsv_inv(bool lower, int n, const Ts* T, int ldt, const double* Dinv,
+                            const double* rhs, double* X, unsigned* flags, int* info,
+                            cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const int nblk = (n + kTsBS - 1) / kTsBS;
-  const size_t smem = sizeof(double) * ((size_t)kTsBS * kTsBS + kTsBS + 4 * kTsBS);
-  cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(unsigned) * (size_t)(nblk + 1), s);
+  const size_t smem = sizeof(double) * ((size_t)kTsBS * kTsBS + kTsBS + 4 * kTsBS + kTsBS);
+  cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(X, 0xff, sizeof(double) * (size_t)n, s);
   if (e != cudaSuccess) return e;
   const uint64_t wait_ns = wait_timeout_ns();
   if (lower) {
     e = ensure_dyn_smem(trsv_inv_kernel<Ts, true>, smem);
     if (e != cudaSuccess) return e;
-    trsv_inv_kernel<Ts, true><<<nblk, 256, smem, s>>>(n, T, ldt, Dinv, X, flags, info, wait_ns);
+    trsv_inv_kernel<Ts, true><<<nblk, 256, smem, s>>>(n, T, ldt, Dinv, rhs, X, flags, info, wait_ns);
   } else {
     e = ensure_dyn_smem(trsv_inv_kernel<Ts, false>, smem);
     if (e != cudaSuccess) return e;
-    trsv_inv_kernel<Ts, false><<<nblk, 256, smem, s>>>(n, T, ldt, Dinv, X, flags, info, wait_ns);
+    trsv_inv_kernel<Ts, false><<<nblk, 256, smem, s>>>(n, T, ldt, Dinv, rhs, X, flags, info, wait_ns);
   }
   count_launch();
   return cudaGetLastError();
 }
-template cudaError_t launch_trsv_inv<float>(bool, int, const float*, int, const double*, double*,
-                                            unsigned*, int*, cudaStream_t);
-template cudaError_t launch_trsv_inv<double>(bool, int, const double*, int, const double*, double*,
-                                             unsigned*, int*, cudaStream_t);
+template cudaError_t launch_trsv_inv<float>(bool, int, const float*, int, const double*,
+                                            const double*, double*, unsigned*, int*, cudaStream_t);
+template cudaError_t launch_trsv_inv<double>(bool, int, const double*, int, const double*,
+                                             const double*, double*, unsigned*, int*, cudaStream_t);
 
 }  // namespace gbla
