@@ -76,7 +76,8 @@ const char *gbla_last_error(void);
  * gbla_launch_count: kernels this library has launched in this process.
  * gbla_prof_enable(mask): bracket every later launch group of the kinds set
  *   in mask (bit k = kind k) with a pair of CUDA events on its stream.
- *   Kinds: 0 panel, 1 laswp, 2 trsm, 3 gemm_simt, 4 gemm_tc, 5 convert,
+ *   Kinds: 0 panel, 1 laswp (records nothing: row interchanges run inside
+ *   the panel launches), 2 trsm, 3 gemm_simt, 4 gemm_tc, 5 convert,
  *   6 trsv, 7 matvec, 8 mgs, 9 gmres_update, 10 permute, 11 copy, 12 batched.
  * gbla_prof_read: number of recorded groups of `kind` and their summed
  *   device time in ms (waits for the events). gbla_prof_reset forgets them.

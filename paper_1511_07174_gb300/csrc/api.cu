@@ -150,15 +150,14 @@ static int ceil_div(int a, int b) { return (a + b - 1) / b; }
 // ----------------------------------------------------------------------------
 // Blocked right-looking LU over a generic storage type. Outer blocks of width
 // nb; inside each, inner panels of width kPanelWidth factored by the
-// cooperative kernel, followed by the inner interchanges, substitution and
-// update restricted to the outer block. After the outer block: interchanges
-// on the rest of the matrix, the U row block, and the trailing update.
+// cooperative kernel (whose interchange CTAs also apply the panel's row swaps
+// to every other column of the matrix), followed by the inner substitution and
+// update restricted to the outer block. After the outer block: the U row block
+// and the trailing update.
 static size_t lu_work_layout(Carver& c, int n, int nb, int prec, LuWork* w) {
   double* slots = c.take<double>(panel_slots_doubles());
-  int* plan = c.take<int>(laswp_plan_ints());
   if (w) {
     w->slots = slots;
-    w->plan = plan;
     w->Ak = w->Bk = nullptr;
     w->eA = w->eB = nullptr;
     w->ldk = 0;

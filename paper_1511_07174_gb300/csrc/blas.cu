@@ -1,6 +1,5 @@
 // Level-3 pieces of the blocked LU (paper section 2, "delayed updating"):
-// row interchanges (laswp), the unit-lower triangular solve of the U row
-// block, the SIMT rank-k update (FP64 / FP32), the precision conversions that
+// the unit-lower triangular solve of the U row block, the SIMT rank-k update (FP64 / FP32), the precision conversions that
 // feed the tensor-core update, and permutation helpers for the solves.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -9,148 +8,6 @@
 #include "internal.h"
 
 namespace gbla {
-
-// ----------------------------------------------------------------------------
-// laswp: apply the interchanges ipiv[k1..k2) (1-based global rows, in order)
-// to the columns [c0, c1) and [c2, c3), in two launches:
-//   plan  -- one warp replays the swaps on row labels (block rows in an array,
-//            rows below the block in a small open-addressing table) and writes
-//            the resulting list of (destination row, source row) moves;
-//   apply -- each warp moves its columns, all loads issued before any store.
-// Rows outside [k, nrows) named by a pivot are ignored.
-constexpr int kSwapMax = 256;   // interchanges per launch
-constexpr int kSwapHash = 1024;
-constexpr int kSwapColsPerCta = 32;
-
-size_t laswp_plan_ints() { return 1 + 4 * (size_t)kSwapMax; }
-
-__global__ void __launch_bounds__(32)
-    laswp_plan_kernel(const int* __restrict__ ipiv, int k1, int k2, int nrows, int* __restrict__ plan) {
-  __shared__ int blk[kSwapMax], piv[kSwapMax];
-  __shared__ int hk[kSwapHash], hv[kSwapHash];
-  __shared__ int slot_of[kSwapMax];
-  __shared__ int s_nout;
-  const int lane = threadIdx.x;
-  const int nk = k2 - k1;
-  for (int i = lane; i < nk; i += 32) {
-    blk[i] = k1 + i;
-    piv[i] = ipiv[k1 + i] - 1;
-  }
-  for (int i = lane; i < kSwapHash; i += 32) hk[i] = -1;
-  __syncwarp();
-  if (lane == 0) {
-    int nout = 0;
-    for (int k = k1; k < k2; ++k) {
-      const int p = piv[k - k1];
-      if (p <= k || p >= nrows) continue;
-      int* a = &blk[k - k1];
-      int* b;
-      if (p < k2) {
-        b = &blk[p - k1];
-      } else {
-        int h = (int)(((unsigned)p * 2654435761u) >> 22) & (kSwapHash - 1);
-        while (hk[h] != -1 && hk[h] != p) h = (h + 1) & (kSwapHash - 1);
-        if (hk[h] == -1) {
-          hk[h] = p;
-          hv[h] = p;
-          slot_of[nout++] = h;
-        }
-        b = &hv[h];
-      }
-      const int t = *a;
-      *a = *b;
-      *b = t;
-    }
-    s_nout = nout;
-  }
-  __syncwarp();
-  // compact the moves: block rows first (ascending), then the rows below
-  int* dst = plan + 1;
-  int* src = plan + 1 + 2 * kSwapMax;
-  int base = 0;
-  for (int i0 = 0; i0 < nk; i0 += 32) {
-    const int i = i0 + lane;
-    const bool mv = i < nk && blk[i] != k1 + i;
-    const unsigned m = __ballot_sync(0xffffffffu, mv);
-    if (mv) {
-      const int pos = base + __popc(m & ((1u << lane) - 1));
-      dst[pos] = k1 + i;
-      src[pos] = blk[i];
-    }
-    base += __popc(m);
-  }
-  const int nout = s_nout;
-  for (int i0 = 0; i0 < nout; i0 += 32) {
-    const int i = i0 + lane;
-    bool mv = false;
-    int h = 0;
-    if (i < nout) {
-      h = slot_of[i];
-      mv = hv[h] != hk[h];
-    }
-    const unsigned m = __ballot_sync(0xffffffffu, mv);
-    if (mv) {
-      const int pos = base + __popc(m & ((1u << lane) - 1));
-      dst[pos] = hk[h];
-      src[pos] = hv[h];
-    }
-    base += __popc(m);
-  }
-  if (lane == 0) plan[0] = base;
-}
-
-template <typename T>
-__global__ void __launch_bounds__(256)
-    laswp_apply_kernel(T* __restrict__ A, int lda, int c0, int c1, int c2, int c3,
-                       const int* __restrict__ plan) {
-  __shared__ int dst[2 * kSwapMax], src[2 * kSwapMax];
-  const int np = plan[0];
-  for (int i = threadIdx.x; i < np; i += blockDim.x) {
-    dst[i] = plan[1 + i];
-    src[i] = plan[1 + 2 * kSwapMax + i];
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int n1 = c1 - c0, n2 = c3 - c2;
-  constexpr int kPer = (2 * kSwapMax + 31) / 32;
-  for (int cc = warp; cc < kSwapColsPerCta; cc += (int)(blockDim.x >> 5)) {
-    const int t = blockIdx.x * kSwapColsPerCta + cc;
-    if (t >= n1 + n2) break;
-    const int col = t < n1 ? c0 + t : c2 + (t - n1);
-    T* a = A + (size_t)col * lda;
-    T v[kPer];
-#pragma unroll
-    for (int q = 0; q < kPer; ++q) {
-      const int i = lane + 32 * q;
-      if (i < np) v[q] = a[src[i]];
-    }
-    __syncwarp();
-#pragma unroll
-    for (int q = 0; q < kPer; ++q) {
-      const int i = lane + 32 * q;
-      if (i < np) a[dst[i]] = v[q];
-    }
-  }
-}
-
-template <typename T>
-cudaError_t launch_laswp(T* A, int lda, int nrows, int c0, int c1, int c2, int c3, const int* ipiv,
-                         int k1, int k2, int* plan, cudaStream_t s) {
-  if (c1 < c0) c1 = c0;
-  if (c3 < c2) c3 = c2;
-  const int ncols = (c1 - c0) + (c3 - c2);
-  if (ncols <= 0 || k2 <= k1) return cudaSuccess;
-  if (k2 - k1 > kSwapMax) return cudaErrorInvalidValue;
-  laswp_plan_kernel<<<1, 32, 0, s>>>(ipiv, k1, k2, nrows, plan);
-  laswp_apply_kernel<T><<<(ncols + kSwapColsPerCta - 1) / kSwapColsPerCta, 256, 0, s>>>(
-      A, lda, c0, c1, c2, c3, plan);
-  count_launch(2);
-  return cudaGetLastError();
-}
-template cudaError_t launch_laswp<double>(double*, int, int, int, int, int, int, const int*, int,
-                                          int, int*, cudaStream_t);
-template cudaError_t launch_laswp<float>(float*, int, int, int, int, int, int, const int*, int, int,
-                                         int*, cudaStream_t);
 
 // ----------------------------------------------------------------------------
 // Low-precision conversion helpers (power-of-two sliver scaling).

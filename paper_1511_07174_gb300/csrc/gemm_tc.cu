@@ -1,20 +1,12 @@
 // Trailing-matrix update of the mixed-precision LU on the 5th-generation tensor
 // cores (paper section 2: the rank-k "delayed update" A22 -= L21 U12).
 //
-// One CTA computes a 128 x 128 tile D = L21_tile * U12_tile with tcgen05.mma
-// (cta_group::1, M = 128, N = 128, K = 16 per instruction for 16-bit operands,
-// 8 for TF32), FP32 accumulator in tensor memory (128 TMEM columns). Operands
-// are K-major copies (one row of K elements per matrix row), loaded by TMA
-// with 128-byte swizzle into a 4-stage shared-memory ring guarded by mbarriers:
-//   warp 0 lane 0  -- TMA producer
-//   warp 1 lane 0  -- MMA issuer (tcgen05.commit frees a stage / signals done)
-//   warps 0..3     -- epilogue: tcgen05.ld of the warp's 32 TMEM lanes, then
-//                     C[row, col] -= D * 2^-eA[row] * 2^-eB[col] on the FP32
-//                     working matrix (column-major; a warp covers 32
-//                     consecutive rows, so every access is one 128-byte line;
-//                     32 columns are loaded before any is stored).
-// Shared memory (3 stages, ~97 KB) and tensor memory (128 columns) leave room
-// for two CTAs per SM, so one CTA's epilogue overlaps the other's MMAs.
+// Output tiles of 128 x 128 are computed with tcgen05.mma (cta_group::1,
+// M = N = 128, K = 16 per instruction for 16-bit operands, 8 for TF32) into an
+// FP32 accumulator in tensor memory. Operands are K-major copies (one row of K
+// elements per matrix row) loaded by TMA with 128-byte swizzle. The epilogue
+// scales the accumulator by 2^-eA[row] * 2^-eB[col] (exact powers of two) and
+// subtracts it from the FP32 working matrix C (column-major).
 // Every mbarrier wait is bounded; a wait that gives up records
 // GBLA_INFO_TIMEOUT, skips the epilogue writes, drains the copies it issued and
 // frees its tensor memory before returning.
@@ -26,9 +18,8 @@
 
 namespace gbla {
 
-constexpr int kTcBM = 128, kTcBN = 128, kTcStages = 3;  // 3 stages: two CTAs fit per SM
+constexpr int kTcBM = 128, kTcBN = 128;
 constexpr int kTcStageBytes = 128 * 128;  // one operand tile: 128 rows x 128 bytes
-constexpr int kTcSmemBytes = 2 * kTcStages * kTcStageBytes + 1024 /*align*/ + 256 /*barriers*/;
 
 GBLA_DEVINL uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -113,20 +104,6 @@ GBLA_DEVINL void mma_commit(uint32_t bar) {
       : "memory");
 }
 
-GBLA_DEVINL void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
-      "%30, %31}, [%32];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
-        "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
-        "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
 GBLA_DEVINL void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
@@ -141,150 +118,9 @@ GBLA_DEVINL void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
 // 2^e for |e| <= 126, built from the exponent field (exact).
 GBLA_DEVINL float pow2f(int e) { return __int_as_float((127 + e) << 23); }
 
-struct TcArgs {
-  int M, N, K;
-  float* C;
-  int ldc;
-  const int* eA;
-  const int* eB;
-  int* info;
-  uint64_t wait_ns;
-};
-
-template <int KIND>
-__global__ void __launch_bounds__(128, 2)
-    gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   TcArgs args) {
-  extern __shared__ unsigned char smraw[];
-  const uint32_t raw = smem_u32(smraw);
-  const uint32_t sbase = (raw + 1023u) & ~1023u;
-  unsigned char* sm = smraw + (sbase - raw);
-  const uint32_t sA = sbase;
-  const uint32_t sB = sbase + kTcStages * kTcStageBytes;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + 2 * kTcStages * kTcStageBytes);
-  const uint32_t bar_full = smem_u32(bars);
-  const uint32_t bar_empty = bar_full + 8 * kTcStages;
-  const uint32_t bar_done = bar_full + 16 * kTcStages;
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * kTcStages + 1);
-  int* s_fail = reinterpret_cast<int*>(tmem_holder + 1);
-  int* s_issued = s_fail + 1;
-  __shared__ float s_sb[kTcBN];  // 2^-eB of the tile's columns
-
-  constexpr int kElem = (KIND == GBLA_PREC_TF32) ? 4 : 2;
-  constexpr int kBK = 128 / kElem;  // elements per 128-byte row
-  constexpr uint32_t kIdesc =
-      make_idesc(KIND == GBLA_PREC_TF32 ? 2u : (KIND == GBLA_PREC_BF16 ? 1u : 0u), kTcBM, kTcBN);
-
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * kTcBM, n0 = blockIdx.y * kTcBN;
-  const int KB = (args.K + kBK - 1) / kBK;
-
-  for (int c = threadIdx.x; c < kTcBN; c += blockDim.x) {
-    const int col = n0 + c;
-    s_sb[c] = (args.eB && col < args.N) ? pow2f(-args.eB[col]) : 1.0f;
-  }
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < kTcStages; ++s) {
-      mbar_init(bar_full + 8 * s, 1);
-      mbar_init(bar_empty + 8 * s, 1);
-    }
-    mbar_init(bar_done, 1);
-    *s_fail = 0;
-    *s_issued = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncwarp();
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(tmem_holder)),
-                 "r"(kTcBN));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem = *tmem_holder;
-
-  if (warp == 0 && lane == 0) {
-    int kb = 0;
-    for (; kb < KB; ++kb) {
-      const int s = kb % kTcStages;
-      const uint32_t ph = (uint32_t)((kb / kTcStages) & 1);
-      if (!mbar_wait_bounded(bar_empty + 8 * s, ph ^ 1u, args.wait_ns)) {
-        atomicExch(s_fail, 1);
-        break;
-      }
-      mbar_expect_tx(bar_full + 8 * s, 2 * kTcStageBytes);
-      tma_load_2d(sA + s * kTcStageBytes, &tmA, kb * kBK, m0, bar_full + 8 * s);
-      tma_load_2d(sB + s * kTcStageBytes, &tmB, kb * kBK, n0, bar_full + 8 * s);
-    }
-    *s_issued = kb;
-  } else if (warp == 1 && lane == 0) {
-    for (int kb = 0; kb < KB; ++kb) {
-      const int s = kb % kTcStages;
-      const uint32_t ph = (uint32_t)((kb / kTcStages) & 1);
-      if (!mbar_wait_bounded(bar_full + 8 * s, ph, args.wait_ns)) {
-        atomicExch(s_fail, 1);
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {
-        const uint64_t ad = make_sdesc(sA + s * kTcStageBytes + kk * 32);
-        const uint64_t bd = make_sdesc(sB + s * kTcStageBytes + kk * 32);
-        mma_issue<KIND>(tmem, ad, bd, kIdesc, (kb > 0 || kk > 0) ? 1u : 0u);
-      }
-      mma_commit(bar_empty + 8 * s);
-    }
-    mma_commit(bar_done);
-  }
-  __syncwarp();
-
-  if (!mbar_wait_bounded(bar_done, 0, args.wait_ns)) atomicExch(s_fail, 1);
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  __syncthreads();
-  const bool fail = *(volatile int*)s_fail != 0;  // uniform across the CTA
-  if (fail) {
-    if (threadIdx.x == 0) {
-      gbla_flag_timeout(args.info);
-      // drain TMA copies that were issued but never consumed
-      const int issued = *(volatile int*)s_issued;
-      for (int kb = (issued > kTcStages ? issued - kTcStages : 0); kb < issued; ++kb)
-        mbar_wait_bounded(bar_full + 8 * (kb % kTcStages), (uint32_t)((kb / kTcStages) & 1),
-                          args.wait_ns);
-    }
-  } else {
-    const int row = m0 + warp * 32 + lane;
-    const bool rok = row < args.M;
-    const float sa = (rok && args.eA) ? pow2f(-args.eA[row]) : 1.0f;
-    float* __restrict__ crow = args.C + row + (size_t)n0 * args.ldc;
-    const int ncol = min(kTcBN, args.N - n0);
-#pragma unroll 1
-    for (int cb = 0; cb < kTcBN; cb += 32) {
-      uint32_t v[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
-      if (rok) {
-        float cv[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-          cv[j] = (cb + j < ncol) ? crow[(size_t)(cb + j) * args.ldc] : 0.0f;
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if (cb + j < ncol)
-            crow[(size_t)(cb + j) * args.ldc] = cv[j] - (__uint_as_float(v[j]) * sa) * s_sb[cb + j];
-      }
-    }
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcBN));
-  }
-}
-
 // ---------------------------------------------------------------------------
-// Persistent, warp-specialised variant: one CTA per SM walks the output tiles
-// (tile t, t + gridDim.x, ...). Warp 0 lane 0 issues TMA loads into a 6-stage
+// Persistent, warp-specialised kernel: one CTA per SM walks the output tiles
+// (tile t, t + gridDim.x, ...). Warp 0 lane 0 issues TMA loads into a 4-stage
 // ring, warp 1 lane 0 issues the MMAs into one of two tensor-memory
 // accumulators (2 x 128 columns), and warps 2-9 run the epilogue of tile i
 // (two warps per 32-lane group of tensor memory, one per half of the columns)

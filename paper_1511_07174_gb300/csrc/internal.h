@@ -100,14 +100,6 @@ template <typename Ts>
 cudaError_t launch_panel(Ts* A, int lda, int m, int w, int row0, int* ipiv, int* info,
                          double* slots, unsigned panel_index, int ncols, cudaStream_t s);
 
-// Interchanges ipiv[k1..k2) (k2 - k1 <= 256) on columns [c0,c1) u [c2,c3);
-// rows outside [k, nrows) named by a pivot are ignored (defensive: never
-// index out of A). plan: laswp_plan_ints() ints of device scratch.
-size_t laswp_plan_ints();
-template <typename T>
-cudaError_t launch_laswp(T* A, int lda, int nrows, int c0, int c1, int c2, int c3, const int* ipiv,
-                         int k1, int k2, int* plan, cudaStream_t s);
-
 // B (w x N, ldb) <- L^{-1} B with L unit lower (w x w, ldl). Tc: arithmetic type.
 // out_kind: 0 none, GBLA_PREC_BF16/FP16/TF32 -> also write a K-major copy of
 // the result (column j at outK + j*ldk, 2- or 4-byte elements) with one
@@ -201,7 +193,6 @@ cudaError_t launch_chol(int n, double* A, int lda, int* info, cudaStream_t s);
 // ---- blocked LU driver (api.cu) ---------------------------------------------
 struct LuWork {
   double* slots;        // panel exchange slots, panel_slots_doubles(), zeroed per factorisation
-  int* plan;            // interchange plan, laswp_plan_ints()
   // mixed path only
   void* Ak;
   void* Bk;

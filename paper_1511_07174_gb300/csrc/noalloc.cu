@@ -21,13 +21,11 @@
 namespace gbla {
 
 // Room for the panel kernel's exchange area on a device with up to
-// kStaticMaxSms multiprocessors (2 * (SMs + 1) slots of kPanelSlotW doubles
-// and a pivot log of one word per panel column), followed by the interchange
-// plan (kStaticPlanInts ints).
+// kStaticMaxSms multiprocessors: 2 * (SMs + 1) slots of kPanelSlotW doubles
+// and a pivot log of one word per panel column.
 constexpr int kStaticMaxSms = 256;
 constexpr size_t kStaticSlotsDoubles = (size_t)2 * (kStaticMaxSms + 1) * kPanelSlotW + kPanelWidth;
-constexpr size_t kStaticPlanInts = 1 + 4 * 256;
-constexpr size_t kStaticTotalDoubles = kStaticSlotsDoubles + (kStaticPlanInts + 1) / 2;
+constexpr size_t kStaticTotalDoubles = kStaticSlotsDoubles;
 constexpr size_t kStaticSlotsBytes = kStaticTotalDoubles * sizeof(double);
 
 static __device__ __align__(256) double g_static_slots[kStaticTotalDoubles];
@@ -72,7 +70,7 @@ extern "C" int gbla_lu_factor_static(int n, double* A, int lda, int* ipiv, int* 
   if (dp.device < 0) return GBLA_ERR_CUDA;
   if (!dp.coop) return GBLA_ERR_DEVICE;
   // the fixed array must hold every slot the panel kernel can use on this device
-  if (panel_slots_doubles() > kStaticSlotsDoubles || laswp_plan_ints() > kStaticPlanInts)
+  if (panel_slots_doubles() > kStaticSlotsDoubles)
     return GBLA_ERR_WORKSPACE;
   cudaError_t e;
   double* slots = static_slots_address(dev, &e);
@@ -86,7 +84,6 @@ extern "C" int gbla_lu_factor_static(int n, double* A, int lda, int* ipiv, int* 
     return GBLA_ERR_CUDA;
   LuWork w;
   w.slots = slots;
-  w.plan = reinterpret_cast<int*>(slots + kStaticSlotsDoubles);
   w.Ak = w.Bk = nullptr;
   w.eA = w.eB = nullptr;
   w.ldk = 0;
