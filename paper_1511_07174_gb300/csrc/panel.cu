@@ -1,5 +1,8 @@
 // Panel factorisation with partial pivoting (paper section 2, the GEPP step of
-// the blocked LU): an m x w panel (w <= 32) is spread over C cooperative CTAs,
+// the blocked LU). Full-width panels of up to 16384 (FP32) or 4096 (FP64)
+// rows run in one thread-block cluster (the cluster variant further down);
+// the kernels described here take the others: an m x w panel (w <= 32) is
+// spread over C cooperative CTAs,
 // each holding a contiguous slab of R rows in shared memory in the storage
 // precision Ts, which is also the arithmetic precision (FP64 for the FP64
 // factorisation; FP32 for the low-precision one, every operation rounded to
@@ -104,6 +107,17 @@ struct PivKey<float> {
     return k ? (int)(0xffffffffu - (unsigned)(k & 0xffffffffull)) : INT_MAX;
   }
   GBLA_DEVINL bool zero_pivot() const { return (k >> 32) == 0; }
+  GBLA_DEVINL bool valid() const { return k != 0; }
+  GBLA_DEVINL bool same(const PivKey& o) const { return k == o.k; }
+  GBLA_DEVINL void to_pair(u64& a, u64& b) const {
+    a = k;
+    b = 0;
+  }
+  GBLA_DEVINL static PivKey from_pair(u64 a, u64) {
+    PivKey p;
+    p.k = a;
+    return p;
+  }
   static constexpr int kWords = 2;
   GBLA_DEVINL void to_words(uint32_t (&w)[2]) const {
     w[0] = (uint32_t)(k & 0xffffffffull);
@@ -140,6 +154,18 @@ struct PivKey<double> {
   }
   GBLA_DEVINL int row() const { return r; }
   GBLA_DEVINL bool zero_pivot() const { return k == 0; }
+  GBLA_DEVINL bool valid() const { return r != INT_MAX; }
+  GBLA_DEVINL bool same(const PivKey& o) const { return k == o.k && r == o.r; }
+  GBLA_DEVINL void to_pair(u64& a, u64& b) const {
+    a = k;
+    b = (u64)(unsigned)r;
+  }
+  GBLA_DEVINL static PivKey from_pair(u64 a, u64 b) {
+    PivKey p;
+    p.k = a;
+    p.r = (int)(unsigned)b;
+    return p;
+  }
   static constexpr int kWords = 3;
   GBLA_DEVINL void to_words(uint32_t (&w)[3]) const {
     w[0] = (uint32_t)(k & 0xffffffffull);
@@ -158,6 +184,27 @@ template <typename Ts>
 GBLA_DEVINL void warp_merge(PivKey<Ts>& p) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) p.shfl_merge(o);
+}
+
+// The same warp-wide argmax with the warp's integer max reduction (redux):
+// the larger |a| bits first, then, among the lanes that hold them, the lower
+// row. Every lane ends with the winning key. All 32 lanes must take part.
+GBLA_DEVINL void warp_merge_redux(PivKey<float>& p) {
+  const uint32_t hi = (uint32_t)(p.k >> 32), lo = (uint32_t)(p.k & 0xffffffffull);
+  const uint32_t mhi = __reduce_max_sync(0xffffffffu, hi);
+  const uint32_t mlo = __reduce_max_sync(0xffffffffu, hi == mhi ? lo : 0u);
+  p.k = ((u64)mhi << 32) | mlo;
+}
+GBLA_DEVINL void warp_merge_redux(PivKey<double>& p) {
+  const uint32_t hi = (uint32_t)(p.k >> 32), lo = (uint32_t)(p.k & 0xffffffffull);
+  const uint32_t mhi = __reduce_max_sync(0xffffffffu, hi);
+  const uint32_t mlo = __reduce_max_sync(0xffffffffu, hi == mhi ? lo : 0u);
+  // among equal |a|, the lowest row: the largest complement (an empty key's
+  // row INT_MAX complements to the smallest value any holder can offer)
+  const bool tie = hi == mhi && lo == mlo;
+  const uint32_t nr = __reduce_max_sync(0xffffffffu, tie ? ~(uint32_t)p.r : 0u);
+  p.k = ((u64)mhi << 32) | mlo;
+  p.r = (int)~nr;
 }
 
 // Interchange role of the panel launch: the last S CTAs apply each column's
@@ -575,6 +622,424 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Cluster variant. The panel rows are spread over the CL CTAs (CL <= 16) of
+// one thread-block cluster, RPT (1 or 2) rows per thread, all kPanelWidth
+// columns in registers; the three argmax levels (thread -> warp -> CTA ->
+// cluster) use the warp's integer max reduction. The per-column exchange stays inside the cluster: every CTA
+// pushes its candidate (pivot key + row) into the shared memory of every CTA
+// of the cluster with st.async, completing bytes on the receiver's mbarrier,
+// and CTA 0 pushes old row j the same way; each CTA then waits on its own
+// mbarrier alone and reduces the CL candidates locally. Nothing goes through
+// global memory except the pivot log read by the interchange CTAs, which form
+// further clusters of the same cooperative launch.
+//
+// Buffers are double-buffered by column parity. A CTA pushes column j + 2
+// only after it has received every CTA's column j + 1 message, and each CTA
+// sends that message only after it has finished reading its column j
+// buffers; a CTA re-arms the mbarrier of column j + 2 before it sends its own
+// column j + 1 message, so the transaction count is always armed before any
+// byte of that column can arrive.
+constexpr int kClMax = 16;
+
+template <typename Ts>
+struct alignas(16) ClMsg {
+  u64 k;                 // pivot key words (PivKey::to_pair)
+  u64 r;
+  Ts v[kPanelWidth];     // the candidate row
+};
+
+GBLA_DEVINL uint32_t cl_smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+GBLA_DEVINL uint32_t cl_mapa(uint32_t a, int rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+GBLA_DEVINL void cl_st_async(uint32_t raddr, uint4 v, uint32_t rbar) {
+  asm volatile(
+      "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(
+          raddr),
+      "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "r"(rbar)
+      : "memory");
+}
+GBLA_DEVINL void cl_mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+GBLA_DEVINL void cl_mbar_arm(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+GBLA_DEVINL bool cl_mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+GBLA_DEVINL bool cl_mbar_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+  if (cl_mbar_try(bar, parity)) return true;
+  const uint64_t t0 = gbla_now_ns();
+  while (!cl_mbar_try(bar, parity))
+    if (gbla_now_ns() - t0 > limit_ns) return false;
+  return true;
+}
+GBLA_DEVINL uint32_t cl_nctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+GBLA_DEVINL uint32_t cl_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+GBLA_DEVINL void cl_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+
+template <typename Ts, int NT, int RPT>
+__global__ void __launch_bounds__(NT, 1)
+    panel_cluster_kernel(Ts* __restrict__ A, int lda, int m, int row0,
+                         int* __restrict__ ipiv, int* __restrict__ info,
+                         double* __restrict__ slots_d, unsigned tag_base, uint64_t wait_ns,
+                         int ncols, int CL) {
+  typedef PivKey<Ts> Key;
+  constexpr int W = kPanelWidth;
+  constexpr int NW = NT / 32;
+  constexpr int NCH = (int)(sizeof(ClMsg<Ts>) / 16);   // 16-byte chunks per message
+  constexpr int NJ = (int)(W * sizeof(Ts) / 16);       // 16-byte chunks of row j
+  __shared__ ClMsg<Ts> s_warp[2][NW];                  // each warp's winner (key + row)
+  __shared__ ClMsg<Ts> s_recv[2][kClMax];              // candidates pushed by the cluster
+  __shared__ alignas(16) Ts s_rowj[2][W];              // row j staged by its owner
+  __shared__ alignas(16) Ts s_rowj_recv[2][W];         // row j pushed by CTA 0
+  __shared__ alignas(8) u64 s_bar[2];
+  __shared__ int s_abort;
+
+  const u64* pivlog_r = reinterpret_cast<const u64*>(slots_d) + panel_pivlog_offset();
+  const int S = (int)gridDim.x - CL;
+  if ((int)blockIdx.x >= CL) {
+    swapper_role<Ts>(A - (size_t)row0 - (size_t)row0 * lda, lda, ncols, row0, W, W,
+                     (int)blockIdx.x - CL, S, pivlog_r, tag_base, info, wait_ns);
+    return;
+  }
+  u64* pivlog = reinterpret_cast<u64*>(slots_d) + panel_pivlog_offset();
+  // every shared-memory address below is mapped into CTAs 0 .. CL - 1 of this
+  // cluster: a launch whose clusters are not CL CTAs wide (never made by this
+  // library's launcher) does no exchange at all and reports a failed wait
+  if (cl_nctarank() != (uint32_t)CL || cl_ctarank() != blockIdx.x) {
+    if (threadIdx.x == 0) gbla_flag_timeout(info);
+    return;
+  }
+  const int c = blockIdx.x;  // rank in the panel cluster (cluster 0)
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int g0 = c * NT * RPT + tid;  // panel row of this thread's row i: g0 + i * NT
+  const uint32_t kExpect = (uint32_t)(CL * sizeof(ClMsg<Ts>) + W * sizeof(Ts));
+
+  Ts a[RPT][W];
+#pragma unroll
+  for (int i = 0; i < RPT; ++i) {
+    const int gi = g0 + i * NT;
+#pragma unroll
+    for (int k = 0; k < W; ++k) a[i][k] = gi < m ? A[(size_t)k * lda + gi] : (Ts)0;
+  }
+  const uint32_t bar[2] = {cl_smem_u32(&s_bar[0]), cl_smem_u32(&s_bar[1])};
+  if (tid == 0) {
+    cl_mbar_init(bar[0], 1);
+    cl_mbar_init(bar[1], 1);
+    cl_mbar_arm(bar[0], kExpect);
+    cl_mbar_arm(bar[1], kExpect);
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // pivots start as "no interchange", so that an aborted launch leaves only
+  // in-range row indices behind for the kernels that follow
+  if (c == 0 && tid < W) ipiv[tid] = row0 + tid + 1;
+  cl_sync();  // every mbarrier initialised and armed before the first push
+
+  bool aborted = false;
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    const int par = j & 1;
+    // 1. candidate of this thread (ties -> lower row), warp argmax; the
+    //    winning lane stages its key and row; thread j of CTA 0 (which owns
+    //    panel row j) stages row j
+    Key bk;
+    int ib = 0;
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+      const int gi = g0 + i * NT;
+      if (gi < m && gi >= j) {
+        const Key ki = Key::make(a[i][j], gi);
+        if (!bk.valid()) {
+          bk = ki;
+          ib = i;
+        } else {
+          Key t = bk;
+          t.merge(ki);
+          if (!t.same(bk)) {
+            bk = ki;
+            ib = i;
+          }
+        }
+      }
+    }
+    Key wk = bk;
+    warp_merge_redux(wk);
+    ClMsg<Ts>& mine = s_warp[par][warp];
+    if (bk.valid() && bk.same(wk)) {
+      bk.to_pair(mine.k, mine.r);
+#pragma unroll
+      for (int i = 0; i < RPT; ++i)
+        if (i == ib) {
+          if constexpr (sizeof(Ts) == 4) {
+#pragma unroll
+            for (int q = 0; q < W / 4; ++q)
+              reinterpret_cast<float4*>(mine.v)[q] =
+                  make_float4(a[i][4 * q], a[i][4 * q + 1], a[i][4 * q + 2], a[i][4 * q + 3]);
+          } else {
+#pragma unroll
+            for (int q = 0; q < W / 2; ++q)
+              reinterpret_cast<double2*>(mine.v)[q] = make_double2(a[i][2 * q], a[i][2 * q + 1]);
+          }
+        }
+    } else if (lane == 0 && !wk.valid()) {
+      Key().to_pair(mine.k, mine.r);
+    }
+    if (c == 0 && tid == j) {
+      if constexpr (sizeof(Ts) == 4) {
+#pragma unroll
+        for (int q = 0; q < W / 4; ++q)
+          reinterpret_cast<float4*>(s_rowj[par])[q] =
+              make_float4(a[0][4 * q], a[0][4 * q + 1], a[0][4 * q + 2], a[0][4 * q + 3]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < W / 2; ++q)
+          reinterpret_cast<double2*>(s_rowj[par])[q] = make_double2(a[0][2 * q], a[0][2 * q + 1]);
+      }
+    }
+    __syncthreads();
+    if (s_abort) {
+      aborted = true;
+      break;
+    }
+    // 2. warp 0: the CTA's winner, pushed to every CTA of the cluster;
+    //    warp 1 of CTA 0: row j, pushed likewise
+    if (warp == 0) {
+      Key ck;
+      if (lane < NW) ck = Key::from_pair(s_warp[par][lane].k, s_warp[par][lane].r);
+      Key mk = ck;
+      warp_merge_redux(mk);
+      const unsigned bal = __ballot_sync(0xffffffffu, lane < NW && mk.valid() && ck.same(mk));
+      const int ww = bal ? __ffs(bal) - 1 : 0;
+      const uint4* src = reinterpret_cast<const uint4*>(&s_warp[par][ww]);
+      const uint32_t dst = cl_smem_u32(&s_recv[par][c]);
+      for (int t = lane; t < CL * NCH; t += 32) {
+        const int d = t / NCH, ch = t - d * NCH;
+        uint4 v = src[ch];
+        if (ch == 0 && !mk.valid()) {
+          u64 k0, r0;
+          Key().to_pair(k0, r0);
+          v = make_uint4((uint32_t)k0, (uint32_t)(k0 >> 32), (uint32_t)r0, (uint32_t)(r0 >> 32));
+        }
+        cl_st_async(cl_mapa(dst + 16u * ch, d), v, cl_mapa(bar[par], d));
+      }
+    } else if (warp == 1 && c == 0) {
+      const uint4* src = reinterpret_cast<const uint4*>(s_rowj[par]);
+      const uint32_t dst = cl_smem_u32(s_rowj_recv[par]);
+      for (int t = lane; t < CL * NJ; t += 32) {
+        const int d = t / NJ, ch = t - d * NJ;
+        cl_st_async(cl_mapa(dst + 16u * ch, d), src[ch], cl_mapa(bar[par], d));
+      }
+    }
+    // 3. wait for the CL candidates and row j; every warp reduces them
+    const bool ok = cl_mbar_wait(bar[par], (uint32_t)((j >> 1) & 1), wait_ns);
+    if (!ok) {
+      s_abort = 1;
+    } else {
+      if (tid == 0 && j + 2 < W) cl_mbar_arm(bar[par], kExpect);
+      Key q;
+      Ts qv = (Ts)0;
+      if (lane < CL) {
+        q = Key::from_pair(s_recv[par][lane].k, s_recv[par][lane].r);
+        qv = s_recv[par][lane].v[j];
+      }
+      // each lane forms the reciprocal of its candidate's pivot while the
+      // warp reduces the keys; the winner's is then broadcast
+      const Ts qr = qv != (Ts)0 ? (Ts)1 / qv : (Ts)0;
+      Key g = q;
+      warp_merge_redux(g);
+      const unsigned bal = __ballot_sync(0xffffffffu, lane < CL && q.same(g));
+      const int cw = bal ? __ffs(bal) - 1 : 0;
+      const int p = g.row();
+      const Ts* prow = s_recv[par][cw].v;
+      const Ts pv = __shfl_sync(0xffffffffu, qv, cw);
+      const Ts rp = __shfl_sync(0xffffffffu, qr, cw);
+      if (c == 0 && tid == 0) {
+        ipiv[j] = row0 + p + 1;
+        if (S > 0)
+          st_relaxed_u64(pivlog + j, ((u64)(tag_base | (unsigned)(j + 1)) << 32) | (u64)(unsigned)p);
+        if (g.zero_pivot()) atomicCAS(info, 0, row0 + j + 1);
+      }
+      // 4. interchange rows j and p, scale by the reciprocal pivot, rank-1
+      //    update (the same operations, in the same order, as the other
+      //    panel kernels)
+#pragma unroll
+      for (int i = 0; i < RPT; ++i) {
+        const int gi = g0 + i * NT;
+        if (gi < m) {
+          // one source row for the interchange, so that only one row of
+          // shared-memory loads is live at a time
+          const Ts* src = (p != j && gi == j) ? prow : ((p != j && gi == p) ? s_rowj_recv[par] : nullptr);
+          if (src) {
+#pragma unroll
+            for (int k = 0; k < W; ++k) a[i][k] = src[k];
+          }
+          if (gi > j) {
+            Ts l = a[i][j];
+            if (pv != (Ts)0) {
+              l = l * rp;
+              a[i][j] = l;
+            }
+#pragma unroll
+            for (int k = j + 1; k < W; ++k) a[i][k] = fma(-l, prow[k], a[i][k]);
+          }
+        }
+      }
+    }
+  }
+  if (!aborted) {
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+      const int gi = g0 + i * NT;
+#pragma unroll
+      for (int k = 0; k < W; ++k)
+        if (gi < m) A[(size_t)k * lda + gi] = a[i][k];
+    }
+  } else if (tid == 0) {
+    gbla_flag_timeout(info);
+  }
+  // no CTA leaves while a peer may still write into its shared memory
+  cl_sync();
+  if (aborted) {
+    const uint64_t t0 = gbla_now_ns();
+    while (gbla_now_ns() - t0 < 20000) {
+    }
+  }
+}
+
+template <typename Ts, int NT, int RPT>
+static cudaError_t launch_panel_cluster_nt(Ts* A, int lda, int m, int row0, int* ipiv,
+                                           int* info, double* slots, unsigned tag_base,
+                                           uint64_t wait_ns, int ncols, int CL, int S,
+                                           cudaStream_t s) {
+  // once per device: allow clusters of 16 and look up how many clusters of
+  // each size can be resident, so that a launch that cannot be co-resident
+  // is never attempted
+  static int max_clusters[64][kClMax + 1];
+  static bool init[64] = {false};
+  const int dev = device_props().device;
+  if (dev < 0 || dev >= 64) return cudaErrorNotSupported;
+  if (!init[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(panel_cluster_kernel<Ts, NT, RPT>,
+                                         cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return cudaErrorNotSupported;
+    }
+    for (int i = 0; i <= kClMax; ++i) max_clusters[dev][i] = -1;
+    init[dev] = true;
+  }
+  if (max_clusters[dev][CL] < 0) {
+    cudaLaunchConfig_t q = {};
+    q.gridDim = dim3((unsigned)CL);
+    q.blockDim = dim3(NT);
+    cudaLaunchAttribute qa[1];
+    qa[0].id = cudaLaunchAttributeClusterDimension;
+    qa[0].val.clusterDim.x = (unsigned)CL;
+    qa[0].val.clusterDim.y = 1;
+    qa[0].val.clusterDim.z = 1;
+    q.attrs = qa;
+    q.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, panel_cluster_kernel<Ts, NT, RPT>, &q) != cudaSuccess) {
+      cudaGetLastError();
+      n = 0;
+    }
+    max_clusters[dev][CL] = n;
+  }
+  if (max_clusters[dev][CL] < 1 + S / CL) return cudaErrorNotSupported;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(CL + S));
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[2];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  at[1].id = cudaLaunchAttributeCooperative;
+  at[1].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 2;
+  count_launch();
+  return cudaLaunchKernelEx(&cfg, panel_cluster_kernel<Ts, NT, RPT>, A, lda, m, row0, ipiv, info,
+                            slots, tag_base, wait_ns, ncols, CL);
+}
+
+// Cluster launch shape for a full-width panel of m >= 32 rows: NT threads
+// per CTA (128, 256 or 512) with RPT rows each (2 only for FP32 panels of
+// more than 8192 rows), CL = the power of two >= m / (NT * RPT), and enough
+// interchange CTAs (a multiple of CL, at most 64) for about one column per
+// thread. An FP64 row takes twice the registers, so FP64 stays at <= 256
+// threads.
+// Returns cudaErrorNotSupported, with nothing enqueued, for a narrower or
+// taller panel or when the device cannot hold the launch.
+template <typename Ts>
+static cudaError_t launch_panel_cluster(Ts* A, int lda, int m, int w, int row0, int* ipiv,
+                                        int* info, double* slots, unsigned tag_base,
+                                        uint64_t wait_ns, int ncols, cudaStream_t s) {
+  constexpr int kMaxNt = sizeof(Ts) == 4 ? 512 : 256;
+  constexpr int kMaxRpt = sizeof(Ts) == 4 ? 2 : 1;
+  if (w != kPanelWidth || m < kPanelWidth) return cudaErrorNotSupported;
+  int NT = 128;
+  while (NT < kMaxNt && (long long)NT * kClMax < m) NT *= 2;
+  const int RPT = (long long)NT * kClMax >= m ? 1 : 2;
+  if (RPT > kMaxRpt || (long long)NT * RPT * kClMax < m) return cudaErrorNotSupported;
+  const int need = (m + NT * RPT - 1) / (NT * RPT);
+  int CL = 1;
+  while (CL < need) CL *= 2;
+  const int other = ncols - w;
+  int S = 0;
+  if (other > 0) {
+    S = (other + NT - 1) / NT;
+    if (S > 64) S = 64;
+    S = ((S + CL - 1) / CL) * CL;
+  }
+  if (RPT == 2) {
+    if constexpr (sizeof(Ts) == 4)
+      return launch_panel_cluster_nt<Ts, 512, 2>(A, lda, m, row0, ipiv, info, slots, tag_base, wait_ns, ncols, CL, S, s);
+    return cudaErrorNotSupported;
+  }
+  switch (NT) {
+    case 128:
+      return launch_panel_cluster_nt<Ts, 128, 1>(A, lda, m, row0, ipiv, info, slots, tag_base, wait_ns, ncols, CL, S, s);
+    case 256:
+      return launch_panel_cluster_nt<Ts, 256, 1>(A, lda, m, row0, ipiv, info, slots, tag_base, wait_ns, ncols, CL, S, s);
+    default:
+      if constexpr (sizeof(Ts) == 4)
+        return launch_panel_cluster_nt<Ts, 512, 1>(A, lda, m, row0, ipiv, info, slots, tag_base, wait_ns, ncols, CL, S, s);
+      return cudaErrorNotSupported;
+  }
+}
+
 template <typename Ts>
 cudaError_t launch_panel(Ts* A, int lda, int m, int w, int row0, int* ipiv, int* info,
                          double* slots, unsigned panel_index, int ncols, cudaStream_t s) {
@@ -582,7 +1047,14 @@ cudaError_t launch_panel(Ts* A, int lda, int m, int w, int row0, int* ipiv, int*
   if (w > kPanelWidth) return cudaErrorInvalidValue;
   const DeviceProps& dp = device_props();
   if (dp.device < 0) return cudaErrorNoDevice;
-  // Up to 64 CTAs: the exchange round per column gets slower with the number
+  {
+    const cudaError_t ec = launch_panel_cluster<Ts>(A, lda, m, w, row0, ipiv, info, slots,
+                                                    (panel_index + 1u) << 6, wait_timeout_ns(),
+                                                    ncols, s);
+    if (ec != cudaErrorNotSupported) return ec;
+  }
+  // Panels taller than one cluster holds: up to 64 CTAs exchanging through
+  // global memory. Up to 64 CTAs: the exchange round per column gets slower with the number
   // of CTAs polling each other's headers, faster than the per-CTA share of
   // the rank-1 update grows (measured at m = 16384: 3.96 us per column with
   // 64 CTAs, 4.79 us with 152).

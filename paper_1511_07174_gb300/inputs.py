@@ -80,8 +80,11 @@ def rhs_from_solution(A, x_true):
     return A @ x_true
 
 
-def dyadic_lu(n, seed):
-    """(A, L, U, perm) with A = P0^t L U, where (P0^t M)[perm[i]] = M[i]."""
+def dyadic_lu(n, seed, device="cpu"):
+    """(A, L, U, perm) with A = P0^t L U, where (P0^t M)[perm[i]] = M[i].
+    The entries are drawn on the CPU; the product (exact in FP64 in any
+    summation order: every partial sum is a multiple of 1/4 below 2^40) is
+    formed on `device`."""
     g = _gen(seed)
     lvals = torch.tensor([0.0, 0.25, -0.25, 0.5, -0.5], dtype=torch.float64)
     L = lvals[torch.randint(0, 5, (n, n), generator=g)]
@@ -90,9 +93,10 @@ def dyadic_lu(n, seed):
     dvals = torch.tensor([1.0, -1.0, 2.0, -2.0, 4.0, -4.0], dtype=torch.float64)
     U = torch.triu(U, 1) + torch.diag(dvals[torch.randint(0, 6, (n,), generator=g)])
     perm = torch.randperm(n, generator=g)
+    L, U = L.to(device), U.to(device)
     M = L @ U
     A = torch.empty_like(M)
-    A[perm] = M
+    A[perm.to(device)] = M
     return A, L, U, perm
 
 

@@ -55,6 +55,22 @@ def test_mixed_dyadic_exact(prec, n, nb):
     assert np.array_equal(oracle.perm_from_ipiv(ipiv, n), perm.numpy())
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp16x3", "bf16"])
+def test_mixed_dyadic_exact_tall_panels(prec):
+    """n = 8448: the first panels (more than 8192 rows) hold two rows per
+    thread in the cluster panel kernel, the later ones one; factors and
+    pivots must still be exact."""
+    n = 8448
+    A, L0, U0, perm = inputs.dyadic_lu(n, seed=611, device=DEV)
+    F, ipiv, info = api.lu_factor_mixed(A, prec=prec, nb=256)
+    assert int(info.item()) == 0
+    Fd = F.to(torch.float64)
+    eye = torch.eye(n, dtype=torch.float64, device=DEV)
+    assert torch.equal(torch.tril(Fd, -1) + eye, L0)
+    assert torch.equal(torch.triu(Fd), U0)
+    assert np.array_equal(oracle.perm_from_ipiv(ipiv.cpu().numpy(), n), perm.numpy())
+
+
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("n,nb", [(300, 64), (1100, 256)])
 def test_mixed_factor_bound_and_oracle(prec, n, nb):
