@@ -54,12 +54,14 @@ GBLA_DEVINL void store_lowp(void* base, size_t row, int K, int k, float v) {
 }
 
 // ----------------------------------------------------------------------------
-// TRSM: B (w x N) <- L^{-1} B, L unit lower w x w. A warp owns 4 columns; lane
-// q*32+l of each column lives in lane l (rows r = lane + 32 q, q < 8, w <= 256).
-// Columns of L are staged through shared memory 32 at a time.
+// TRSM: B (w x N) <- L^{-1} B, L unit lower w x w. A warp owns 4 columns; row
+// r = lane + 32 q (q < Q, w <= 32 Q) of each column lives in lane `lane`.
+// Columns of L are staged through shared memory 32 at a time. The loop over
+// those 32-row chunks is unrolled, so every register index is a constant and
+// a chunk only updates the row groups at or below it.
 constexpr int kTrsmCols = 32;  // columns per CTA (8 warps x 4)
 
-template <typename Ts, typename Tc, int OUT>
+template <typename Ts, typename Tc, int OUT, int Q>
 __global__ void __launch_bounds__(256)
     trsm_lunit_kernel(const Ts* __restrict__ L, int ldl, Ts* __restrict__ B, int ldb, int w, int N,
                       void* __restrict__ outK, int ldk, int* __restrict__ outE) {
@@ -67,9 +69,9 @@ __global__ void __launch_bounds__(256)
   Tc* Ls = reinterpret_cast<Tc*>(smraw);  // [32][w]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int col0 = blockIdx.x * kTrsmCols + warp * 4;
-  Tc x[8][4];
+  Tc x[Q][4];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
+  for (int q = 0; q < Q; ++q) {
     const int r = lane + 32 * q;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -77,43 +79,36 @@ __global__ void __launch_bounds__(256)
       x[q][c] = (r < w && col < N) ? (Tc)B[r + (size_t)col * ldb] : (Tc)0;
     }
   }
-  for (int i0 = 0; i0 < w; i0 += 32) {
-    __syncthreads();
-    {
-      // all loads of the chunk are issued before any shared-memory store
-      constexpr int kMaxPer = 32 * 256 / 256;
-      Ts v[kMaxPer];
 #pragma unroll
-      for (int t = 0; t < kMaxPer; ++t) {
-        const int idx = threadIdx.x + 256 * t;
-        const int cc = idx / w, r = idx - cc * w, i = i0 + cc;
-        v[t] = (idx < 32 * w && i < w && r > i) ? L[r + (size_t)i * ldl] : (Ts)0;
-      }
+  for (int qi = 0; qi < Q; ++qi) {
+    const int i0 = 32 * qi;
+    if (i0 < w) {
+      __syncthreads();
+      {
+        // all loads of the chunk are issued before any shared-memory store
+        constexpr int kPer = 4 * Q;  // 32 x (32 Q) elements over 256 threads
+        Ts v[kPer];
 #pragma unroll
-      for (int t = 0; t < kMaxPer; ++t) {
-        const int idx = threadIdx.x + 256 * t;
-        if (idx < 32 * w) Ls[idx] = (Tc)v[t];
-      }
-    }
-    __syncthreads();
-    const int qi = i0 >> 5;
-    const int iend = min(32, w - i0);
-    for (int ii = 0; ii < iend; ++ii) {
-      Tc xi[4];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) xi[c] = (Tc)0;
-#pragma unroll
-      for (int q = 0; q < 8; ++q)
-        if (q == qi) {
-#pragma unroll
-          for (int c = 0; c < 4; ++c) xi[c] = x[q][c];
+        for (int t = 0; t < kPer; ++t) {
+          const int idx = threadIdx.x + 256 * t;
+          const int cc = idx / w, r = idx - cc * w, i = i0 + cc;
+          v[t] = (idx < 32 * w && i < w && r > i) ? L[r + (size_t)i * ldl] : (Ts)0;
         }
 #pragma unroll
-      for (int c = 0; c < 4; ++c) xi[c] = __shfl_sync(0xffffffffu, xi[c], ii);
-      const Tc* lcol = Ls + ii * w;
+        for (int t = 0; t < kPer; ++t) {
+          const int idx = threadIdx.x + 256 * t;
+          if (idx < 32 * w) Ls[idx] = (Tc)v[t];
+        }
+      }
+      __syncthreads();
+      const int iend = min(32, w - i0);
+      for (int ii = 0; ii < iend; ++ii) {
+        Tc xi[4];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        if (q >= qi) {
+        for (int c = 0; c < 4; ++c) xi[c] = __shfl_sync(0xffffffffu, x[qi][c], ii);
+        const Tc* lcol = Ls + ii * w;
+#pragma unroll
+        for (int q = qi; q < Q; ++q) {
           const int r = lane + 32 * q;
           const Tc l = r < w ? lcol[r] : (Tc)0;
 #pragma unroll
@@ -127,7 +122,7 @@ __global__ void __launch_bounds__(256)
     const int col = col0 + c;
     float mx = 0.0f;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < Q; ++q) {
       const int r = lane + 32 * q;
       if (r < w && col < N) {
         const Ts v = (Ts)x[q][c];
@@ -141,7 +136,7 @@ __global__ void __launch_bounds__(256)
       if (col < N) {
         if (lane == 0) outE[col] = e;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
+        for (int q = 0; q < Q; ++q) {
           const int r = lane + 32 * q;
           if (r < w) store_lowp<OUT, false>(outK, (size_t)col * ldk, w, r, ldexpf((float)(Ts)x[q][c], e));
         }
@@ -150,40 +145,53 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-template <typename Ts, typename Tc>
-cudaError_t launch_trsm_lunit(const Ts* L, int ldl, Ts* B, int ldb, int w, int N, int out_kind,
-                              void* outK, int ldk, int* outE, cudaStream_t s) {
-  if (w <= 0 || N <= 0) return cudaSuccess;
-  if (w > 256) return cudaErrorInvalidValue;
+template <typename Ts, typename Tc, int Q>
+static cudaError_t trsm_dispatch(const Ts* L, int ldl, Ts* B, int ldb, int w, int N, int out_kind,
+                                 void* outK, int ldk, int* outE, cudaStream_t s) {
   const size_t smem = (size_t)32 * w * sizeof(Tc);
   const dim3 grid((N + kTrsmCols - 1) / kTrsmCols);
-#define GBLA_TRSM_CASE(K, IDX)                                                       \
-  {                                                                                \
-    auto kfn = trsm_lunit_kernel<Ts, Tc, K>;                                       \
-    cudaError_t ea = ensure_dyn_smem(kfn, smem);                                   \
-    if (ea != cudaSuccess) return ea;                                              \
-    kfn<<<grid, 256, smem, s>>>(L, ldl, B, ldb, w, N, outK, ldk, outE);            \
-    break;                                                                         \
+#define GBLA_TRSM_CASE(K)                                                  \
+  {                                                                      \
+    auto kfn = trsm_lunit_kernel<Ts, Tc, K, Q>;                          \
+    cudaError_t ea = ensure_dyn_smem(kfn, smem);                         \
+    if (ea != cudaSuccess) return ea;                                    \
+    kfn<<<grid, 256, smem, s>>>(L, ldl, B, ldb, w, N, outK, ldk, outE);  \
+    break;                                                               \
   }
-  switch (out_kind) {
-    case 0: GBLA_TRSM_CASE(0, 0)
-    case GBLA_PREC_BF16: GBLA_TRSM_CASE(GBLA_PREC_BF16, 1)
-    case GBLA_PREC_FP16: GBLA_TRSM_CASE(GBLA_PREC_FP16, 2)
-    case GBLA_PREC_TF32: GBLA_TRSM_CASE(GBLA_PREC_TF32, 3)
-    case GBLA_PREC_FP16X3: GBLA_TRSM_CASE(GBLA_PREC_FP16X3, 4)
-    case GBLA_PREC_BF16X3: GBLA_TRSM_CASE(GBLA_PREC_BF16X3, 5)
-    default: return cudaErrorInvalidValue;
+  if constexpr (sizeof(Ts) == 8) {
+    // the low-precision copies exist for FP32 storage only
+    switch (out_kind) {
+      case 0: GBLA_TRSM_CASE(0)
+      default: return cudaErrorInvalidValue;
+    }
+  } else {
+    switch (out_kind) {
+      case 0: GBLA_TRSM_CASE(0)
+      case GBLA_PREC_BF16: GBLA_TRSM_CASE(GBLA_PREC_BF16)
+      case GBLA_PREC_FP16: GBLA_TRSM_CASE(GBLA_PREC_FP16)
+      case GBLA_PREC_TF32: GBLA_TRSM_CASE(GBLA_PREC_TF32)
+      case GBLA_PREC_FP16X3: GBLA_TRSM_CASE(GBLA_PREC_FP16X3)
+      case GBLA_PREC_BF16X3: GBLA_TRSM_CASE(GBLA_PREC_BF16X3)
+      default: return cudaErrorInvalidValue;
+    }
   }
 #undef GBLA_TRSM_CASE
   count_launch();
   return cudaGetLastError();
 }
+
+template <typename Ts, typename Tc>
+cudaError_t launch_trsm_lunit(const Ts* L, int ldl, Ts* B, int ldb, int w, int N, int out_kind,
+                              void* outK, int ldk, int* outE, cudaStream_t s) {
+  if (w <= 0 || N <= 0) return cudaSuccess;
+  if (w > 256) return cudaErrorInvalidValue;
+  if (w <= 32) return trsm_dispatch<Ts, Tc, 1>(L, ldl, B, ldb, w, N, out_kind, outK, ldk, outE, s);
+  return trsm_dispatch<Ts, Tc, 8>(L, ldl, B, ldb, w, N, out_kind, outK, ldk, outE, s);
+}
 template cudaError_t launch_trsm_lunit<double, double>(const double*, int, double*, int, int, int,
                                                        int, void*, int, int*, cudaStream_t);
 template cudaError_t launch_trsm_lunit<float, float>(const float*, int, float*, int, int, int, int,
                                                      void*, int, int*, cudaStream_t);
-template cudaError_t launch_trsm_lunit<float, double>(const float*, int, float*, int, int, int,
-                                                      int, void*, int, int*, cudaStream_t);
 
 // ----------------------------------------------------------------------------
 // SIMT GEMM: C = alpha * A * op(B) + beta * C. Thread (tx, ty) owns rows
