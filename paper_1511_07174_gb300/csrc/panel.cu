@@ -657,12 +657,17 @@ GBLA_DEVINL uint32_t cl_mapa(uint32_t a, int rank) {
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
   return r;
 }
-GBLA_DEVINL void cl_st_async(uint32_t raddr, uint4 v, uint32_t rbar) {
+// Bulk copy of `bytes` (a multiple of 16) from this CTA's shared memory to
+// another CTA's, completing the bytes on that CTA's mbarrier.
+GBLA_DEVINL void cl_bulk_push(uint32_t rdst, uint32_t src, uint32_t bytes, uint32_t rbar) {
   asm volatile(
-      "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(
-          raddr),
-      "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "r"(rbar)
+      "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          rdst),
+      "r"(src), "r"(bytes), "r"(rbar)
       : "memory");
+}
+GBLA_DEVINL void cl_fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 GBLA_DEVINL void cl_mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
@@ -712,8 +717,6 @@ __global__ void __launch_bounds__(NT, 1)
   typedef PivKey<Ts> Key;
   constexpr int W = kPanelWidth;
   constexpr int NW = NT / 32;
-  constexpr int NCH = (int)(sizeof(ClMsg<Ts>) / 16);   // 16-byte chunks per message
-  constexpr int NJ = (int)(W * sizeof(Ts) / 16);       // 16-byte chunks of row j
   __shared__ ClMsg<Ts> s_warp[2][NW];                  // each warp's winner (key + row)
   __shared__ ClMsg<Ts> s_recv[2][kClMax];              // candidates pushed by the cluster
   __shared__ alignas(16) Ts s_rowj[2][W];              // row j staged by its owner
@@ -809,8 +812,10 @@ __global__ void __launch_bounds__(NT, 1)
               reinterpret_cast<double2*>(mine.v)[q] = make_double2(a[i][2 * q], a[i][2 * q + 1]);
           }
         }
+      cl_fence_proxy_async();  // the bulk copies read the staged message
     } else if (lane == 0 && !wk.valid()) {
       Key().to_pair(mine.k, mine.r);
+      cl_fence_proxy_async();
     }
     if (c == 0 && tid == j) {
       if constexpr (sizeof(Ts) == 4) {
@@ -823,14 +828,16 @@ __global__ void __launch_bounds__(NT, 1)
         for (int q = 0; q < W / 2; ++q)
           reinterpret_cast<double2*>(s_rowj[par])[q] = make_double2(a[0][2 * q], a[0][2 * q + 1]);
       }
+      cl_fence_proxy_async();
     }
     __syncthreads();
     if (s_abort) {
       aborted = true;
       break;
     }
-    // 2. warp 0: the CTA's winner, pushed to every CTA of the cluster;
-    //    warp 1 of CTA 0: row j, pushed likewise
+    // 2. warp 0: the CTA's winner (its staged message; a CTA without
+    //    candidates has every warp's entry empty and sends entry 0), one bulk
+    //    copy per CTA of the cluster; warp 1 of CTA 0: row j, likewise
     if (warp == 0) {
       Key ck;
       if (lane < NW) ck = Key::from_pair(s_warp[par][lane].k, s_warp[par][lane].r);
@@ -838,25 +845,13 @@ __global__ void __launch_bounds__(NT, 1)
       warp_merge_redux(mk);
       const unsigned bal = __ballot_sync(0xffffffffu, lane < NW && mk.valid() && ck.same(mk));
       const int ww = bal ? __ffs(bal) - 1 : 0;
-      const uint4* src = reinterpret_cast<const uint4*>(&s_warp[par][ww]);
-      const uint32_t dst = cl_smem_u32(&s_recv[par][c]);
-      for (int t = lane; t < CL * NCH; t += 32) {
-        const int d = t / NCH, ch = t - d * NCH;
-        uint4 v = src[ch];
-        if (ch == 0 && !mk.valid()) {
-          u64 k0, r0;
-          Key().to_pair(k0, r0);
-          v = make_uint4((uint32_t)k0, (uint32_t)(k0 >> 32), (uint32_t)r0, (uint32_t)(r0 >> 32));
-        }
-        cl_st_async(cl_mapa(dst + 16u * ch, d), v, cl_mapa(bar[par], d));
-      }
+      if (lane < CL)
+        cl_bulk_push(cl_mapa(cl_smem_u32(&s_recv[par][c]), lane), cl_smem_u32(&s_warp[par][ww]),
+                     (uint32_t)sizeof(ClMsg<Ts>), cl_mapa(bar[par], lane));
     } else if (warp == 1 && c == 0) {
-      const uint4* src = reinterpret_cast<const uint4*>(s_rowj[par]);
-      const uint32_t dst = cl_smem_u32(s_rowj_recv[par]);
-      for (int t = lane; t < CL * NJ; t += 32) {
-        const int d = t / NJ, ch = t - d * NJ;
-        cl_st_async(cl_mapa(dst + 16u * ch, d), src[ch], cl_mapa(bar[par], d));
-      }
+      if (lane < CL)
+        cl_bulk_push(cl_mapa(cl_smem_u32(s_rowj_recv[par]), lane), cl_smem_u32(s_rowj[par]),
+                     (uint32_t)(W * sizeof(Ts)), cl_mapa(bar[par], lane));
     }
     // 3. wait for the CL candidates and row j; every warp reduces them
     const bool ok = cl_mbar_wait(bar[par], (uint32_t)((j >> 1) & 1), wait_ns);
@@ -890,9 +885,13 @@ __global__ void __launch_bounds__(NT, 1)
       // 4. interchange rows j and p, scale by the reciprocal pivot, rank-1
       //    update (the same operations, in the same order, as the other
       //    panel kernels)
+      bool below[RPT];
+      Ts lm[RPT];
 #pragma unroll
       for (int i = 0; i < RPT; ++i) {
         const int gi = g0 + i * NT;
+        below[i] = false;
+        lm[i] = (Ts)0;
         if (gi < m) {
           // one source row for the interchange, so that only one row of
           // shared-memory loads is live at a time
@@ -907,8 +906,34 @@ __global__ void __launch_bounds__(NT, 1)
               l = l * rp;
               a[i][j] = l;
             }
+            below[i] = true;
+            lm[i] = l;
+          }
+        }
+      }
+      // the pivot row is read 16 bytes at a time, once for all rows of the thread
+      constexpr int VE = 16 / (int)sizeof(Ts);
 #pragma unroll
-            for (int k = j + 1; k < W; ++k) a[i][k] = fma(-l, prow[k], a[i][k]);
+      for (int qv4 = (j + 1) / VE; qv4 < W / VE; ++qv4) {
+        Ts pk[VE];
+        if constexpr (sizeof(Ts) == 4) {
+          const float4 v = reinterpret_cast<const float4*>(prow)[qv4];
+          pk[0] = v.x;
+          pk[1] = v.y;
+          pk[2] = v.z;
+          pk[3] = v.w;
+        } else {
+          const double2 v = reinterpret_cast<const double2*>(prow)[qv4];
+          pk[0] = v.x;
+          pk[1] = v.y;
+        }
+#pragma unroll
+        for (int e = 0; e < VE; ++e) {
+          const int k = VE * qv4 + e;
+          if (k > j) {
+#pragma unroll
+            for (int i = 0; i < RPT; ++i)
+              if (below[i]) a[i][k] = fma(-lm[i], pk[e], a[i][k]);
           }
         }
       }
