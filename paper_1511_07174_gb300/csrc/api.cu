@@ -152,7 +152,7 @@ static int ceil_div(int a, int b) { return (a + b - 1) / b; }
 // nb; inside each, inner panels of width kPanelWidth factored by the
 // cooperative kernel (whose interchange CTAs also apply the panel's row swaps
 // to every other column of the matrix), followed by the inner substitution and
-// update restricted to the outer block. After the outer block: the U row block
+// update restricted to the outer block (one fused launch). After the outer block: the U row block
 // and the trailing update.
 static size_t lu_work_layout(Carver& c, int n, int nb, int prec, LuWork* w) {
   double* slots = c.take<double>(panel_slots_doubles());
@@ -184,6 +184,7 @@ template <typename Ts>
 cudaError_t blocked_lu(int n, Ts* A, int lda, int* ipiv, int* info, int nb, int prec,
                               const LuWork& w, cudaStream_t s) {
   typedef Ts Tc_trsm;  // substitution arithmetic: FP64 for FP64 storage, FP32 for FP32
+  unsigned* inner_ctr = reinterpret_cast<unsigned*>(w.slots + kPanelExchangeDoubles + kPanelWidth);
   cudaError_t e;
   for (int k0 = 0; k0 < n; k0 += nb) {
     const int kb = std::min(nb, n - k0);
@@ -194,7 +195,12 @@ cudaError_t blocked_lu(int n, Ts* A, int lda, int* ipiv, int* info, int nb, int 
                                          w.slots, (unsigned)(j0 / kPanelWidth), n, s));
       if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
       const int nrest = k0 + kb - j0 - jb;
-      if (nrest > 0) {
+      if (nrest > 0 && jb == kPanelWidth) {
+        // U12 of the panel and the update of the rest of the outer block, one launch
+        PROF(KK_GEMM_SIMT, s, launch_inner_update<Ts>(n - j0 - jb, nrest, A + j0 + (size_t)j0 * lda, lda,
+                                                      inner_ctr, s));
+        if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
+      } else if (nrest > 0) {
         PROF(KK_TRSM, s, (launch_trsm_lunit<Ts, Tc_trsm>(A + j0 + (size_t)j0 * lda, lda,
                                            A + j0 + (size_t)(j0 + jb) * lda, lda, jb, nrest, 0,
                                            nullptr, 0, nullptr, s)));

@@ -194,6 +194,129 @@ template cudaError_t launch_trsm_lunit<float, float>(const float*, int, float*, 
                                                      void*, int, int*, cudaStream_t);
 
 // ----------------------------------------------------------------------------
+// Inner step of the blocked LU, fused into one launch: U12 = L11^{-1} A12 and
+// A22 -= L21 U12 for a 32-column panel. CTA (x, y) owns the 64 x 64 tile
+// (x, y) of A22; it solves the 64 columns of U12 above its tile itself (a
+// 32 x 32 x 64 / 2 FMA right-looking solve, small next to the tile's
+// update), in the same order of operations as the separate substitution
+// kernel, so the results are those of the two-kernel sequence. The last CTA
+// of a column of tiles to have read A12 (one counter per column of tiles)
+// writes U12 back and clears its counter, so no CTA ever reads a solved
+// value as input and no CTA waits for another.
+template <typename T>
+__global__ void __launch_bounds__(256)
+    inner_update_kernel(int M, int N, T* __restrict__ P, int lda, unsigned* __restrict__ counters) {
+  constexpr int BM = 64, BN = 64, K = kPanelWidth, TM = 4, TN = 4, RX = BM / TM, RY = BN / TN;
+  __shared__ T Ls[K][K + 1];   // strictly lower part of L11
+  __shared__ T Us[K][BN + 1];  // A12 tile, then U12 tile
+  __shared__ T As[K][BM + 1];  // L21 tile, k-major
+  __shared__ int s_last;
+  const int tid = threadIdx.x;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  T* A12 = P + (size_t)K * lda;
+  const T* A21 = P + K;
+  T* A22 = P + K + (size_t)K * lda;
+  {
+    // all global loads are issued before any shared-memory store
+    T vl[K * K / 256], vu[K * BN / 256], va[BM * K / 256];
+#pragma unroll
+    for (int t = 0; t < K * K / 256; ++t) {
+      const int idx = tid + 256 * t, i = idx % K, k = idx / K;
+      vl[t] = i > k ? P[i + (size_t)k * lda] : (T)0;
+    }
+#pragma unroll
+    for (int t = 0; t < K * BN / 256; ++t) {
+      const int idx = tid + 256 * t, k = idx % K, n = n0 + idx / K;
+      vu[t] = n < N ? A12[k + (size_t)n * lda] : (T)0;
+    }
+#pragma unroll
+    for (int t = 0; t < BM * K / 256; ++t) {
+      const int idx = tid + 256 * t, m = m0 + idx % BM, k = idx / BM;
+      va[t] = m < M ? A21[m + (size_t)k * lda] : (T)0;
+    }
+#pragma unroll
+    for (int t = 0; t < K * K / 256; ++t) {
+      const int idx = tid + 256 * t;
+      Ls[idx % K][idx / K] = vl[t];
+    }
+#pragma unroll
+    for (int t = 0; t < K * BN / 256; ++t) {
+      const int idx = tid + 256 * t;
+      Us[idx % K][idx / K] = vu[t];
+    }
+#pragma unroll
+    for (int t = 0; t < BM * K / 256; ++t) {
+      const int idx = tid + 256 * t;
+      As[idx / BM][idx % BM] = va[t];
+    }
+  }
+  __syncthreads();
+  if (tid == 0) s_last = atomicAdd(&counters[blockIdx.y], 1u) == gridDim.x - 1;
+  if (tid < BN) {
+    // column tid of U12: u_i -= l_ik u_k for k = 0, 1, ... (unit diagonal)
+    T u[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) u[k] = Us[k][tid];
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int i = k + 1; i < K; ++i) u[i] = fma(-Ls[i][k], u[k], u[i]);
+#pragma unroll
+    for (int k = 0; k < K; ++k) Us[k][tid] = u[k];
+  }
+  __syncthreads();
+  if (s_last) {
+    for (int idx = tid; idx < K * BN; idx += 256) {
+      const int k = idx % K, n = n0 + idx / K;
+      if (n < N) A12[k + (size_t)n * lda] = Us[k][idx / K];
+    }
+    if (tid == 0) counters[blockIdx.y] = 0u;
+  }
+  const int tx = tid % RX, ty = tid / RX;
+  T acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = (T)0;
+#pragma unroll 8
+  for (int kk = 0; kk < K; ++kk) {
+    T a[TM], b[TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i) a[i] = As[kk][tx + i * RX];
+#pragma unroll
+    for (int j = 0; j < TN; ++j) b[j] = Us[kk][ty + j * RY];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+  }
+#pragma unroll
+  for (int j = 0; j < TN; ++j) {
+    const int n = n0 + ty + j * RY;
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+      const int m = m0 + tx + i * RX;
+      if (m < M && n < N) {
+        T* c = A22 + m + (size_t)n * lda;
+        *c = fma((T)-1, acc[i][j], *c);
+      }
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_inner_update(int M, int N, T* P, int lda, unsigned* counters, cudaStream_t s) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  const dim3 grid((M + 63) / 64, (N + 63) / 64);
+  if ((int)grid.y > kInnerCounters) return cudaErrorInvalidValue;
+  inner_update_kernel<T><<<grid, 256, 0, s>>>(M, N, P, lda, counters);
+  count_launch();
+  return cudaGetLastError();
+}
+template cudaError_t launch_inner_update<double>(int, int, double*, int, unsigned*, cudaStream_t);
+template cudaError_t launch_inner_update<float>(int, int, float*, int, unsigned*, cudaStream_t);
+
+// ----------------------------------------------------------------------------
 // SIMT GEMM: C = alpha * A * op(B) + beta * C. Thread (tx, ty) owns rows
 // tx + i*(BM/TM) and columns ty + j*(BN/TN) of the tile, so that the lanes of
 // a warp touch consecutive rows of column-major C.

@@ -87,6 +87,12 @@ inline int prec_kmult(int p) { return prec_is_split(p) ? 3 : 1; }
 // ---- kernel launchers (all stream-ordered; return cudaError_t) -------------
 constexpr int kPanelWidth = 32;  // inner panel width handled by the cooperative kernel
 constexpr int kPanelSlotW = 72;  // doubles per published candidate slot
+// Layout of the panel scratch (panel_slots_doubles() doubles, zeroed once per
+// factorisation): exchange slots for up to 256 SMs, the pivot log of one
+// panel (kPanelWidth words), then kInnerCounters words for the fused inner
+// update's per-column-tile counters.
+constexpr size_t kPanelExchangeDoubles = (size_t)2 * (256 + 1) * kPanelSlotW;
+constexpr int kInnerCounters = 64;
 
 // Exchange area of the panel kernel (slots for up to 256 SMs + pivot log).
 // It must be zeroed once before the first panel of a factorisation;
@@ -107,6 +113,13 @@ cudaError_t launch_panel(Ts* A, int lda, int m, int w, int row0, int* ipiv, int*
 template <typename Ts, typename Tc>
 cudaError_t launch_trsm_lunit(const Ts* L, int ldl, Ts* B, int ldb, int w, int N, int out_kind,
                               void* outK, int ldk, int* outE, cudaStream_t s);
+
+// Inner step of the blocked LU for a 32-column panel whose top-left element
+// is P: U12 = L11^{-1} A12 (L11 the unit lower 32 x 32 block at P, A12 the
+// 32 x N block right of it) and A22 -= L21 U12 (M x N, below A12), in one
+// launch. counters: kInnerCounters zeroed words (left zeroed on return).
+template <typename T>
+cudaError_t launch_inner_update(int M, int N, T* P, int lda, unsigned* counters, cudaStream_t s);
 
 // C = alpha * A * op(B) + beta * C (column-major). transB: op(B) = B^t with B
 // stored N x K. lower: only elements with row >= col are written.

@@ -21,10 +21,11 @@
 namespace gbla {
 
 // Room for the panel kernel's exchange area on a device with up to
-// kStaticMaxSms multiprocessors: 2 * (SMs + 1) slots of kPanelSlotW doubles
-// and a pivot log of one word per panel column.
+// kStaticMaxSms multiprocessors: 2 * (SMs + 1) slots of kPanelSlotW doubles,
+// a pivot log of one word per panel column and the inner update's counters.
 constexpr int kStaticMaxSms = 256;
-constexpr size_t kStaticSlotsDoubles = (size_t)2 * (kStaticMaxSms + 1) * kPanelSlotW + kPanelWidth;
+constexpr size_t kStaticSlotsDoubles =
+    (size_t)2 * (kStaticMaxSms + 1) * kPanelSlotW + kPanelWidth + kInnerCounters / 2;
 constexpr size_t kStaticTotalDoubles = kStaticSlotsDoubles;
 constexpr size_t kStaticSlotsBytes = kStaticTotalDoubles * sizeof(double);
 

@@ -36,12 +36,7 @@ namespace gbla {
 constexpr int kPanelThreads = 256;
 constexpr int kSlotRow = 4;  // words before the row words in a slot (3 header words + pad)
 
-size_t panel_slots_doubles() {
-  const DeviceProps& p = device_props();
-  int c = p.num_sms > 0 ? p.num_sms : 160;
-  (void)c;
-  return (size_t)2 * (256 + 1) * kPanelSlotW + kPanelWidth;  // slots for <= 256 SMs + pivot log
-}
+size_t panel_slots_doubles() { return kPanelExchangeDoubles + kPanelWidth + kInnerCounters / 2; }
 
 typedef unsigned long long u64;
 
