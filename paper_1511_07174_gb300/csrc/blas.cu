@@ -555,17 +555,23 @@ cudaError_t launch_copy_d2f(const double* A, int lda, float* F, int ldf, int m, 
 }
 
 // ----------------------------------------------------------------------------
-// perm from sequential interchanges: (P v)[i] = v[perm[i]]. One thread applies
-// the n swaps in order on a shared-memory (or, for very large n, global) array.
+// perm from sequential interchanges: (P v)[i] = v[perm[i]]. The pivots are
+// staged in shared memory by the whole block (when both arrays fit), then one
+// thread applies the n swaps in order; every access of that loop is to shared
+// memory. For very large n the arrays stay in global memory.
 __global__ void ipiv_to_perm_kernel(int n, const int* __restrict__ ipiv, int* __restrict__ perm,
                                     int use_smem) {
   extern __shared__ int sp[];
   int* p = use_smem ? sp : perm;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = i;
+  const int* piv = use_smem ? sp + n : ipiv;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    p[i] = i;
+    if (use_smem) sp[n + i] = ipiv[i];
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int j = 0; j < n; ++j) {
-      const int k = ipiv[j] - 1;
+      const int k = piv[j] - 1;
       if (k != j && k > j && k < n) {  // out-of-range pivots are ignored
         const int t = p[j];
         p[j] = p[k];
@@ -581,7 +587,7 @@ __global__ void ipiv_to_perm_kernel(int n, const int* __restrict__ ipiv, int* __
 cudaError_t launch_ipiv_to_perm(int n, const int* ipiv, int* perm, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const DeviceProps& dp = device_props();
-  const size_t bytes = (size_t)n * sizeof(int);
+  const size_t bytes = (size_t)2 * n * sizeof(int);
   const int use_smem = bytes + 1024 <= dp.smem_optin ? 1 : 0;
   if (use_smem) {
     cudaError_t ea = ensure_dyn_smem(ipiv_to_perm_kernel, bytes);
