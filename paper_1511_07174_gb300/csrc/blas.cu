@@ -1,6 +1,8 @@
 // Level-3 pieces of the blocked LU (paper section 2, "delayed updating"):
-// the unit-lower triangular solve of the U row block, the SIMT rank-k update (FP64 / FP32), the precision conversions that
-// feed the tensor-core update, and permutation helpers for the solves.
+// the unit-lower triangular solve of the U row block, the fused inner step
+// (solve and update inside an outer block), the SIMT rank-k update (FP64 /
+// FP32), the precision conversions that feed the tensor-core update, and
+// permutation helpers for the solves.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
