@@ -556,6 +556,33 @@ def secondary(args, pk):
             entry["frac_of_fp64_dgemm"] = entry["tflops"] / fp64_peak
         out[name] = entry
         del bl
+    # batched Cholesky on SPD systems of the same sizes (A_i^t A_i / n_i + I), FP64
+    Sp = [(Ab.t() @ Ab) / Ab.shape[0] + torch.eye(Ab.shape[0], dtype=torch.float64) for Ab in As]
+    flops_c = sum(1.0 / 3.0 * m ** 3 + 2.0 * m * m * k for m, k in zip(sizes, nrhs))
+    bc = BatchedLU(Sp, Bs_, dtype=torch.float64, method="chol")
+    bc.autotune()
+    bc.capture()
+    bc.replay()
+    ms_gc = _event_ms(bc.replay, reps=3)
+    bc.restore()
+    api.prof_enable(["batched"])
+    api.prof_reset()
+    bc.run()
+    torch.cuda.synchronize()
+    cnt, ms_kc = api.prof_read("batched")
+    api.prof_enable([])
+    resc, infoc = bc.results()
+    worst = 0.0
+    for (_, _, Xb), Ab, Bb in zip(resc[:512], Sp[:512], Bs_[:512]):
+        worst = max(worst, float(oracle.backward_error(np.asfortranarray(Ab.numpy()), Xb.numpy(),
+                                                       Bb.numpy()).max()))
+    kc = ms_kc / max(cnt, 1)
+    out["batched_chol_fp64"] = {"systems": len(sizes), "graph_ms": ms_gc, "kernel_ms": kc,
+                                "systems_per_s": len(sizes) / (kc * 1e-3),
+                                "tflops": flops_c / (kc * 1e-3) / 1e12,
+                                "launch_shape": [bc.threads, bc.ctas_per_sm],
+                                "info_nonzero": int((infoc != 0).sum()), "beta_max_first512": worst}
+    del bc, Sp
     # differentiable solve n = 4096, 8 RHS: forward and backward
     A, b, g = inputs.autograd_problem(4096, 8, device=dev)
     Ar = A.clone().requires_grad_(True)

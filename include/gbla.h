@@ -243,6 +243,30 @@ int gbla_lu_solve_batched_f32(int batch, const int *d_n, float *const *d_A, cons
                               int threads, int ctas_per_sm, void *d_work, size_t work_bytes,
                               gbla_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Batched Cholesky + solve (step a9 for symmetric positive definite systems:
+ * A = L L^t and the two substitutions of paper section 2, for every system of
+ * a batch) in ONE persistent kernel launch, with the launch structure of
+ * gbla_lu_solve_batched (same counter-driven grid, same shared-memory /
+ * in-place split, no host synchronisation, no allocation, graph-capturable).
+ * Only the lower triangle of each A is read and overwritten by L; the strict
+ * upper triangle is untouched. d_info[i] = j + 1 when the j-th leading minor
+ * of system i is not positive (its factorisation stops there and its
+ * right-hand sides are left unchanged), else 0. d_nrhs may be NULL (factor
+ * only); at most 4 right-hand sides per system. Workspace:
+ * gbla_chol_batched_workspace(batch) bytes, 256-byte aligned.
+ * Returns -i for an invalid i-th argument, GBLA_ERR_WORKSPACE, GBLA_ERR_CUDA.
+ * ------------------------------------------------------------------------ */
+size_t gbla_chol_batched_workspace(int batch);
+int gbla_chol_solve_batched(int batch, const int *d_n, double *const *d_A, const int *d_lda,
+                            const int *d_nrhs, double *const *d_B, const int *d_ldb, int *d_info,
+                            const int *d_order, int max_n, int threads, int ctas_per_sm,
+                            void *d_work, size_t work_bytes, gbla_stream_t stream);
+int gbla_chol_solve_batched_f32(int batch, const int *d_n, float *const *d_A, const int *d_lda,
+                                const int *d_nrhs, float *const *d_B, const int *d_ldb, int *d_info,
+                                const int *d_order, int max_n, int threads, int ctas_per_sm,
+                                void *d_work, size_t work_bytes, gbla_stream_t stream);
+
 /*
  * Rank-k product C = alpha * U V^t + beta * C (FP64; U m x k, V n x k, C m x n;
  * beta = 0 overwrites C without reading it). With alpha = -1, beta = 0,

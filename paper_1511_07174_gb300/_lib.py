@@ -58,6 +58,9 @@ _SIGS = {
     "gbla_lu_batched_workspace": ([_i], _sz),
     "gbla_lu_solve_batched": ([_i] + [_vp] * 9 + [_i, _i, _i, _vp, _sz, _vp], _i),
     "gbla_lu_solve_batched_f32": ([_i] + [_vp] * 9 + [_i, _i, _i, _vp, _sz, _vp], _i),
+    "gbla_chol_batched_workspace": ([_i], _sz),
+    "gbla_chol_solve_batched": ([_i] + [_vp] * 8 + [_i, _i, _i, _vp, _sz, _vp], _i),
+    "gbla_chol_solve_batched_f32": ([_i] + [_vp] * 8 + [_i, _i, _i, _vp, _sz, _vp], _i),
     "gbla_rank_k_update": ([_i, _i, _i, _d, _vp, _i, _vp, _i, _d, _vp, _i, _vp], _i),
     "gbla_backward_error_workspace": ([_i, _i], _sz),
     "gbla_backward_error": ([_i, _i, _vp, _i, _vp, _i, _vp, _i, _vp, _vp, _sz, _vp], _i),

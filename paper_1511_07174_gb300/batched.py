@@ -1,11 +1,11 @@
-"""Batched LU + solve of many small systems of uneven size (one persistent
-launch, replayable as a CUDA graph) and the autotuner that picks its launch
-shape.
+"""Batched LU (or Cholesky) + solve of many small systems of uneven size (one
+persistent launch, replayable as a CUDA graph) and the autotuner that picks
+its launch shape.
 
 BatchedLU packs the systems into two flat device buffers (column-major
 matrices and right-hand sides), builds the device pointer / size arrays the C
-ABI takes (gbla_lu_solve_batched[_f32]), orders the systems largest first and
-calls the library. The autotuner times the candidate launch shapes (threads
+ABI takes (gbla_lu_solve_batched[_f32], or gbla_chol_solve_batched[_f32] with
+method="chol"), orders the systems largest first and calls the library. The autotuner times the candidate launch shapes (threads
 per CTA x CTAs per SM) on the actual batch and remembers the fastest per GPU,
 dtype and batch profile in a JSON cache.
 """
@@ -48,7 +48,10 @@ def _store_cache(cache):
 
 
 class BatchedLU:
-    def __init__(self, As, Bs=None, dtype=torch.float64, device="cuda"):
+    def __init__(self, As, Bs=None, dtype=torch.float64, device="cuda", method="lu"):
+        if method not in ("lu", "chol"):
+            raise ValueError("method must be 'lu' or 'chol'")
+        self.method = method
         self.dtype = dtype
         self.device = torch.device(device)
         self.sizes = [int(A.shape[0]) for A in As]
@@ -92,7 +95,8 @@ class BatchedLU:
         self.d_order = torch.tensor(order, dtype=torch.int32, device=dev)
         self.max_n = max(self.sizes, default=0)
         L = _lib.load()
-        self.ws = _ws(L.gbla_lu_batched_workspace(self.batch), dev)
+        wsf = L.gbla_lu_batched_workspace if method == "lu" else L.gbla_chol_batched_workspace
+        self.ws = _ws(wsf(self.batch), dev)
         self.threads, self.ctas_per_sm = 256, 1
         self.graph = None
 
@@ -105,16 +109,21 @@ class BatchedLU:
     def run(self, threads=None, ctas_per_sm=None):
         """Factor and solve every system (one kernel launch on the current stream)."""
         L = _lib.load()
-        fn = L.gbla_lu_solve_batched if self.dtype == torch.float64 else L.gbla_lu_solve_batched_f32
         t = self.threads if threads is None else threads
         c = self.ctas_per_sm if ctas_per_sm is None else ctas_per_sm
         p = lambda x: ctypes.c_void_p(x.data_ptr()) if x is not None else ctypes.c_void_p(0)
         has_b = self.nrhs is not None
-        _check("gbla_lu_solve_batched",
-               fn(self.batch, p(self.d_n), p(self.d_A), p(self.d_lda), p(self.d_ipiv),
-                  p(self.d_nrhs) if has_b else ctypes.c_void_p(0), p(self.d_B) if has_b else ctypes.c_void_p(0),
-                  p(self.d_ldb) if has_b else ctypes.c_void_p(0), p(self.info), p(self.d_order),
-                  self.max_n, t, c, p(self.ws), self.ws.numel(), _stream()))
+        rhs = (p(self.d_nrhs) if has_b else ctypes.c_void_p(0), p(self.d_B) if has_b else ctypes.c_void_p(0),
+               p(self.d_ldb) if has_b else ctypes.c_void_p(0))
+        tail = (p(self.info), p(self.d_order), self.max_n, t, c, p(self.ws), self.ws.numel(), _stream())
+        if self.method == "lu":
+            fn = L.gbla_lu_solve_batched if self.dtype == torch.float64 else L.gbla_lu_solve_batched_f32
+            _check("gbla_lu_solve_batched",
+                   fn(self.batch, p(self.d_n), p(self.d_A), p(self.d_lda), p(self.d_ipiv), *rhs, *tail))
+        else:
+            fn = L.gbla_chol_solve_batched if self.dtype == torch.float64 else L.gbla_chol_solve_batched_f32
+            _check("gbla_chol_solve_batched",
+                   fn(self.batch, p(self.d_n), p(self.d_A), p(self.d_lda), *rhs, *tail))
 
     def capture(self):
         """Record restore + run as a CUDA graph (after one eager run, so that every
@@ -140,7 +149,7 @@ class BatchedLU:
     def key(self):
         name = torch.cuda.get_device_name(self.device)
         prof = (self.batch, min(self.sizes, default=0), self.max_n, sum(n ** 3 for n in self.sizes) // (1 << 20))
-        return "%s|%s|%d|%d|%d|%d" % ((name, str(self.dtype)) + prof)
+        return "%s|%s|%s|%d|%d|%d|%d" % ((name, self.method, str(self.dtype)) + prof)
 
     def autotune(self, reps=2, use_cache=True):
         """Time every candidate (threads, CTAs per SM) on this batch; keep the fastest."""
@@ -175,14 +184,16 @@ class BatchedLU:
 
     # -- results -----------------------------------------------------------------
     def results(self):
-        """Lists of (LU, ipiv, X) per system as CPU tensors (A[i, j] indexing), and info."""
+        """Lists of (LU, ipiv, X) per system as CPU tensors (A[i, j] indexing), and info.
+        For method "chol" the first item holds L in its lower triangle (the strict
+        upper triangle is the input's) and ipiv is None."""
         A = self.A.cpu()
         B = self.B.cpu()
         P = self.ipiv.cpu()
         out = []
         for i, n in enumerate(self.sizes):
             LU = A[self.offA[i]:self.offA[i] + n * n].reshape(n, n).t()
-            piv = P[self.offP[i]:self.offP[i] + n]
+            piv = P[self.offP[i]:self.offP[i] + n] if self.method == "lu" else None
             X = None
             if self.nrhs is not None:
                 k = self.nrhs[i]

@@ -532,6 +532,53 @@ int gbla_lu_solve_batched_f32(int batch, const int* d_n, float* const* d_A, cons
                                  max_n, threads, ctas_per_sm, d_work, work_bytes, stream);
 }
 
+}  // extern "C"
+
+template <typename T>
+static int chol_batched_entry(int batch, const int* d_n, T* const* d_A, const int* d_lda,
+                              const int* d_nrhs, T* const* d_B, const int* d_ldb, int* d_info,
+                              const int* d_order, int max_n, int threads, int ctas_per_sm,
+                              void* d_work, size_t work_bytes, gbla_stream_t stream) {
+  clear_error();
+  if (batch < 0) return -1;
+  if (batch > 0 && !d_n) return -2;
+  if (batch > 0 && !d_A) return -3;
+  if (batch > 0 && !d_lda) return -4;
+  if (d_nrhs && (!d_B || !d_ldb)) return -6;
+  if (max_n < 0) return -10;
+  if (threads != 0 && (threads % 32 != 0 || threads < 32 || threads > 1024)) return -11;
+  if (ctas_per_sm < 0 || ctas_per_sm > 32) return -12;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!d_work || !aligned256(d_work)) return GBLA_ERR_WORKSPACE;
+  Carver c(d_work, work_bytes);
+  unsigned* counter = c.take<unsigned>(1);
+  if (!c.ok) return GBLA_ERR_WORKSPACE;
+  if (batch == 0) return GBLA_OK;
+  GBLA_TRYK(KK_BATCHED, s, launch_chol_batched<T>(batch, d_n, d_A, d_lda, d_nrhs, d_B, d_ldb, d_info,
+                                                d_order, max_n, threads, ctas_per_sm, counter, s));
+  return GBLA_OK;
+}
+
+extern "C" {
+
+size_t gbla_chol_batched_workspace(int batch) { return gbla_lu_batched_workspace(batch); }
+
+int gbla_chol_solve_batched(int batch, const int* d_n, double* const* d_A, const int* d_lda,
+                            const int* d_nrhs, double* const* d_B, const int* d_ldb, int* d_info,
+                            const int* d_order, int max_n, int threads, int ctas_per_sm,
+                            void* d_work, size_t work_bytes, gbla_stream_t stream) {
+  return chol_batched_entry<double>(batch, d_n, d_A, d_lda, d_nrhs, d_B, d_ldb, d_info, d_order,
+                                    max_n, threads, ctas_per_sm, d_work, work_bytes, stream);
+}
+
+int gbla_chol_solve_batched_f32(int batch, const int* d_n, float* const* d_A, const int* d_lda,
+                                const int* d_nrhs, float* const* d_B, const int* d_ldb, int* d_info,
+                                const int* d_order, int max_n, int threads, int ctas_per_sm,
+                                void* d_work, size_t work_bytes, gbla_stream_t stream) {
+  return chol_batched_entry<float>(batch, d_n, d_A, d_lda, d_nrhs, d_B, d_ldb, d_info, d_order,
+                                   max_n, threads, ctas_per_sm, d_work, work_bytes, stream);
+}
+
 // ---------------------------------------------------------------------------
 int gbla_rank_k_update(int m, int n, int k, double alpha, const double* U, int ldu, const double* V,
                        int ldv, double beta, double* C, int ldc, gbla_stream_t stream) {

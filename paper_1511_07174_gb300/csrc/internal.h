@@ -200,6 +200,11 @@ cudaError_t launch_lu_batched(int batch, const int* n, T* const* A, const int* l
                               const int* order, int max_n, int threads, int ctas_per_sm,
                               unsigned* counter, cudaStream_t s);
 
+template <typename T>
+cudaError_t launch_chol_batched(int batch, const int* n, T* const* A, const int* lda, const int* nrhs,
+                                T* const* B, const int* ldb, int* info, const int* order, int max_n,
+                                int threads, int ctas_per_sm, unsigned* counter, cudaStream_t s);
+
 // ---- Cholesky (chol.cu) ------------------------------------------------------
 cudaError_t launch_chol(int n, double* A, int lda, int* info, cudaStream_t s);
 

@@ -1,4 +1,4 @@
-"""Batched LU + solve (one persistent launch) against the oracle, system by system.
+"""Batched LU (and Cholesky) + solve (one persistent launch) against the oracle, system by system.
 
 FP64: pivots identical (tie-free inputs), factors within 1e-11 * max|LU|,
 solutions within 1e-10 relative of the oracle's and backward error <= 1e-14.
@@ -110,3 +110,74 @@ def test_batched_4096_uneven(dtype):
         # diagonally dominant: partial pivoting keeps the diagonal
         assert np.array_equal(piv.numpy(), np.arange(1, A.shape[0] + 1))
     assert worst <= 1.0
+
+
+# ------------------------------------------------------------------ Cholesky
+def _spd_batch(seed, count=30):
+    g = torch.Generator().manual_seed(seed)
+    sizes = [1, 2, 17, 255, 256, 300] + torch.randint(3, 260, (count - 6,), generator=g).tolist()
+    As, Bs = [], []
+    for n in sizes:
+        Bm = torch.randn((n, n), generator=g, dtype=torch.float64)
+        As.append(Bm @ Bm.t() / n + torch.eye(n, dtype=torch.float64))
+        Bs.append(torch.randn((n, int(torch.randint(1, 5, (1,), generator=g))), generator=g,
+                              dtype=torch.float64))
+    return As, Bs
+
+
+def test_batched_chol_fp64_matches_oracle():
+    """L within 1e-12 max|L| of the oracle's, strict upper triangle untouched,
+    solutions within 1e-10 relative and backward error <= 1e-14 (shared-memory
+    and in-place paths, n = 1 and ragged sizes)."""
+    As, Bs = _spd_batch(11)
+    bl = BatchedLU(As, Bs, dtype=torch.float64, method="chol")
+    bl.restore()
+    bl.run()
+    torch.cuda.synchronize()
+    res, info = bl.results()
+    for (Lf, piv, X), A, B, inf in zip(res, As, Bs, info.tolist()):
+        An = np.asfortranarray(A.numpy())
+        Lo, info_o = oracle.potrf(An)
+        assert inf == info_o == 0 and piv is None
+        Lg = Lf.numpy()
+        assert np.abs(np.tril(Lg) - np.tril(Lo)).max() <= 1e-12 * max(1.0, np.abs(np.tril(Lo)).max())
+        assert np.array_equal(np.triu(Lg, 1), np.triu(A.numpy(), 1))
+        Xo = oracle.potrs(Lo, B.numpy())
+        assert np.abs(X.numpy() - Xo).max() <= 1e-10 * max(1.0, np.abs(Xo).max())
+        assert oracle.backward_error(An, X.numpy(), B.numpy()).max() <= 1e-14
+
+
+def test_batched_chol_fp32_and_not_spd():
+    """FP32: backward error (FP64 on the FP32 solution) <= 64 n u32; a system
+    whose third leading minor is negative reports info = 3 and keeps its
+    right-hand sides; the others are unaffected; a graph replay reproduces
+    the eager run bit for bit."""
+    As, Bs = _spd_batch(12, count=12)
+    bad = As[5].clone()
+    bad[2, 2] = -1.0
+    As[5] = bad
+    bl = BatchedLU(As, Bs, dtype=torch.float32, method="chol")
+    bl.restore()
+    bl.run()
+    torch.cuda.synchronize()
+    eagerA, eagerB, info_e = bl.A.clone(), bl.B.clone(), bl.info.clone()
+    res, info = bl.results()
+    for i, ((Lf, piv, X), A, B) in enumerate(zip(res, As, Bs)):
+        n = A.shape[0]
+        A32 = A.to(torch.float32).to(torch.float64).numpy()
+        B32 = B.to(torch.float32)
+        _, info_o = oracle.potrf(np.asfortranarray(A32))
+        assert int(info[i]) == info_o
+        if i == 5:
+            assert info_o == 3
+            assert torch.equal(X, B32)
+            continue
+        beta = oracle.backward_error(np.asfortranarray(A32), X.to(torch.float64).numpy(),
+                                     B32.to(torch.float64).numpy()).max()
+        assert beta <= 64 * n * 2.0 ** -24
+    bl.capture()
+    bl.replay()
+    torch.cuda.synchronize()
+    torch.testing.assert_close(bl.A, eagerA, rtol=0, atol=0, equal_nan=True)
+    torch.testing.assert_close(bl.B, eagerB, rtol=0, atol=0, equal_nan=True)
+    assert torch.equal(bl.info, info_e)
