@@ -337,13 +337,27 @@ def run_ours(args, ws, rank):
     del As, bs
     torch.cuda.synchronize()
     barrier(ws)
+    # the inputs of system k + 1 travel on a copy stream while system k is solved
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
-    t0.record()
-    for _ in range(args.e2e_steps):
-        for k in range(nsys):
+    main = torch.cuda.current_stream()
+    copy_s = torch.cuda.Stream()
+    copied = [torch.cuda.Event() for _ in range(nsys)]
+
+    def fetch(k):
+        with torch.cuda.stream(copy_s):
             dA[k].copy_(hostA[k], non_blocking=True)
             db[k].copy_(hostb[k], non_blocking=True)
+            copied[k].record(copy_s)
+
+    t0.record()
+    for _ in range(args.e2e_steps):
+        copy_s.wait_stream(main)  # after t0, and after the previous step has read the buffers
+        fetch(0)
+        for k in range(nsys):
+            if k + 1 < nsys:
+                fetch(k + 1)
+            main.wait_event(copied[k])
             Fk, ipiv, info = api.lu_factor_mixed(dA[k], prec=args.prec, nb=args.nb, F=F)
             x, st = api.gmresir(dA[k], Fk, ipiv, db[k], tol=1e-14, max_outer=20,
                                 restart_m=args.restart)
