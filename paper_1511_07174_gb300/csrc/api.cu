@@ -145,8 +145,6 @@ static int cuda_status_at(cudaError_t e, const char* what, int line) {
 
 static bool aligned256(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 255) == 0; }
 
-static int ceil_div(int a, int b) { return (a + b - 1) / b; }
-
 // ----------------------------------------------------------------------------
 // Blocked right-looking LU over a generic storage type. Outer blocks of width
 // nb; inside each, inner panels of width kPanelWidth factored by the

@@ -10,7 +10,6 @@ namespace gbla {
 
 constexpr int kResRows = 256;   // rows per CTA (one thread per row)
 constexpr int kResCols = 512;   // columns per CTA
-constexpr int kResNR = 8;       // right-hand sides per pass
 
 size_t residual_work_doubles(int n, int nrhs) {
   const size_t chunks = (size_t)((n + kResCols - 1) / kResCols);

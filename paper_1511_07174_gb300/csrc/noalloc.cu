@@ -28,6 +28,7 @@ constexpr size_t kStaticSlotsDoubles =
     (size_t)2 * (kStaticMaxSms + 1) * kPanelSlotW + kPanelWidth + kInnerCounters / 2;
 constexpr size_t kStaticTotalDoubles = kStaticSlotsDoubles;
 constexpr size_t kStaticSlotsBytes = kStaticTotalDoubles * sizeof(double);
+static_assert(kStaticSlotsBytes < 300 * 1024, "the fixed scratch is meant to stay below 300 KiB");
 
 static __device__ __align__(256) double g_static_slots[kStaticTotalDoubles];
 

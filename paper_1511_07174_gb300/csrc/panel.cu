@@ -252,8 +252,11 @@ __global__ void __launch_bounds__(kPanelThreads)
   Ts* slab = reinterpret_cast<Ts*>(smem);       // [w][R], column-major slab
   Ts* prow = slab + (size_t)w * R;              // pivot row (w)
   Ts* rj = prow + kPanelWidth;                  // old row j (w)
-  __shared__ Key s_wk[kPanelThreads / 32];
-  __shared__ Key s_key;
+  // raw storage: a __shared__ object is never constructed
+  __shared__ alignas(16) unsigned char s_wk_raw[sizeof(Key) * (kPanelThreads / 32)];
+  __shared__ alignas(16) unsigned char s_key_raw[sizeof(Key)];
+  Key* s_wk = reinterpret_cast<Key*>(s_wk_raw);
+  Key& s_key = *reinterpret_cast<Key*>(s_key_raw);
   __shared__ Ts s_rp;
   __shared__ int s_abort;
 
@@ -428,8 +431,11 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
   constexpr int KW = Key::kWords;
   constexpr int W = kPanelWidth;
   __shared__ Ts prow[W], rj[W], crow[W], jrow[W];
-  __shared__ Key s_wk[kPanelThreads / 32];
-  __shared__ Key s_key;
+  // raw storage: a __shared__ object is never constructed
+  __shared__ alignas(16) unsigned char s_wk_raw[sizeof(Key) * (kPanelThreads / 32)];
+  __shared__ alignas(16) unsigned char s_key_raw[sizeof(Key)];
+  Key* s_wk = reinterpret_cast<Key*>(s_wk_raw);
+  Key& s_key = *reinterpret_cast<Key*>(s_key_raw);
   __shared__ Ts s_rp;
   __shared__ int s_abort;
 
