@@ -175,8 +175,18 @@ def gmresir(A, F, ipiv, b, tol=1e-14, inner_tol=1e-8, max_outer=10, restart_m=50
 
 
 def solve_mixed(A, b, prec="bf16", nb=256, **kw):
-    """Mixed-precision LU + GMRES-IR. Returns (x, stats)."""
+    """Mixed-precision LU + GMRES-IR. Returns (x, stats). For a 2-D b (n x k) the
+    matrix is factored once and every column is refined on its own: x is n x k and
+    stats a list of k dicts."""
     F, ipiv, info = lu_factor_mixed(A, prec, nb)
+    if b.dim() == 2:
+        xs, sts = [], []
+        for j in range(b.shape[1]):
+            x, st = gmresir(A, F, ipiv, b[:, j], **kw)
+            st["info"] = int(info.item())
+            xs.append(x)
+            sts.append(st)
+        return torch.stack(xs, dim=1), sts
     x, st = gmresir(A, F, ipiv, b, **kw)
     st["info"] = int(info.item())
     return x, st

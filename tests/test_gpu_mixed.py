@@ -109,3 +109,19 @@ def test_gmresir_small(prec, kappa):
     LUo, ipo, _ = oracle.getrf(An)
     xo = oracle.getrs(LUo, ipo, b.numpy())[:, 0]
     assert np.abs(xg - xo).max() <= kappa * 1e-13 * np.abs(xo).max()
+
+
+def test_solve_mixed_several_rhs():
+    """One factorisation, three right-hand sides refined one by one: each column
+    reaches backward error <= 1e-14 (oracle FP64 matvec)."""
+    n = 600
+    A = inputs.haar_kappa(n, 1e2, device=DEV)
+    X0 = inputs.normal((n, 3), 6, DEV)
+    B = A @ X0
+    X, sts = api.solve_mixed(A, B, prec="fp16x3", nb=128, max_outer=20)
+    assert X.shape == (n, 3) and len(sts) == 3
+    An = np.asfortranarray(A.cpu().numpy())
+    for j in range(3):
+        assert sts[j]["converged"]
+        assert oracle.backward_error(An, X[:, j].cpu().numpy(), B[:, j].cpu().numpy())[0] <= 1e-14
+
