@@ -62,3 +62,26 @@ def test_workspace_sizes(lib):
     assert lib.gbla_lu_factor_mixed_workspace(1000, 256, 3) > lib.gbla_lu_factor_workspace(1000, 256)
     assert lib.gbla_gmresir_workspace(1000, 50) >= 1000 * 51 * 8
     assert lib.gbla_lu_solve_workspace(100, 4) >= 100 * 4 * 8
+
+
+def test_batched_arguments_rejected_on_host(lib):
+    v = ctypes.c_void_p(0)
+    fake = ctypes.c_void_p(256)
+    ws = lib.gbla_chol_batched_workspace(8)
+    assert ws > 0 and lib.gbla_lu_batched_workspace(8) > 0
+    assert lib.gbla_chol_batched_workspace(-1) == 0
+    # batch < 0; missing sizes, matrices, leading dimensions; rhs without B
+    assert lib.gbla_chol_solve_batched(-1, v, v, v, v, v, v, v, v, 0, 0, 0, fake, ws, v) == -1
+    assert lib.gbla_chol_solve_batched(2, v, fake, fake, v, v, v, v, v, 0, 0, 0, fake, ws, v) == -2
+    assert lib.gbla_chol_solve_batched(2, fake, v, fake, v, v, v, v, v, 0, 0, 0, fake, ws, v) == -3
+    assert lib.gbla_chol_solve_batched(2, fake, fake, v, v, v, v, v, v, 0, 0, 0, fake, ws, v) == -4
+    assert lib.gbla_chol_solve_batched_f32(2, fake, fake, fake, fake, v, fake, v, v, 0, 0, 0, fake, ws, v) == -6
+    # launch-shape knobs and workspace
+    assert lib.gbla_chol_solve_batched(2, fake, fake, fake, v, v, v, v, v, -1, 0, 0, fake, ws, v) == -10
+    assert lib.gbla_chol_solve_batched(2, fake, fake, fake, v, v, v, v, v, 0, 48, 0, fake, ws, v) == -11
+    assert lib.gbla_chol_solve_batched(2, fake, fake, fake, v, v, v, v, v, 0, 0, 33, fake, ws, v) == -12
+    assert lib.gbla_chol_solve_batched(2, fake, fake, fake, v, v, v, v, v, 0, 0, 0, v, ws, v) == 1001
+    # an empty batch is a no-op that touches nothing
+    assert lib.gbla_chol_solve_batched(0, v, v, v, v, v, v, v, v, 0, 0, 0, fake, ws, v) == 0
+    assert lib.gbla_lu_solve_batched(-1, v, v, v, v, v, v, v, v, v, 0, 0, 0, fake, ws, v) == -1
+    assert lib.gbla_lu_solve_batched(2, fake, fake, fake, v, v, v, v, v, v, 0, 0, 0, fake, ws, v) == -5
