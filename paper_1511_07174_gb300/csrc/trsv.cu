@@ -387,7 +387,14 @@ cudaError_t launch_trsv_inv(bool lower, int n, const Ts* T, int ldt, const doubl
                             cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const int nblk = (n + kTsBS - 1) / kTsBS;
-  const size_t smem = sizeof(double) * ((size_t)kTsBS * kTsBS + kTsBS + 4 * kTsBS + kTsBS);
+  // One CTA per SM: the late blocks of the chain are bound by the SM's FP64
+  // rate, which two resident blocks would share. Asking for more than half
+  // of an SM's shared memory keeps a second CTA off the SM; the blocks that do
+  // not fit start as the early ones finish (in ticket order, so every block a
+  // CTA waits for has started before it).
+  const DeviceProps& dp = device_props();
+  size_t smem = sizeof(double) * ((size_t)kTsBS * kTsBS + kTsBS + 4 * kTsBS + kTsBS);
+  if (dp.smem_optin > 2 * smem) smem = dp.smem_optin / 2 + 1024;
   cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(X, 0xff, sizeof(double) * (size_t)n, s);
