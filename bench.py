@@ -213,6 +213,16 @@ def oracle_sample(A_host, ksteps):
 
 
 # ---------------------------------------------------------------- reference arm
+def bench_config(args, nsys, ws):
+    """The workload both arms are quoted on."""
+    n = args.n
+    return {"workload": "dense LU solve n=%d, 3 systems (kappa 1e2, 1e4, 1e6; Haar U,V; "
+                        "geometric singular values), 1 RHS each, to backward error 1e-14" % n,
+            "n": n, "prec": args.prec, "nb": args.nb, "restart": args.restart,
+            "systems_per_step": nsys, "parallelism": "replicas" if ws > 1 else "single",
+            "l2": "no flush: each FP64 matrix (%.1f GiB) exceeds L2" % (n * n * 8 / 2 ** 30)}
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -236,7 +246,7 @@ def run_reference(args, ws, rank):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": tmean * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "n=%d dense LU with partial pivoting (oracle sample)" % n, "n": n},
+            "config": bench_config(args, len(KAPPAS), 1),
             "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
@@ -443,12 +453,7 @@ def run_ours(args, ws, rank):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "%s update, f32 factors, f64 refinement" % args.prec, "data": "synthetic",
-            "config": {"workload": "dense LU solve n=%d, 3 systems (kappa 1e2, 1e4, 1e6; Haar U,V; "
-                                   "geometric singular values), 1 RHS each, to backward error 1e-14"
-                                   % n,
-                       "n": n, "prec": args.prec, "nb": args.nb, "restart": args.restart,
-                       "systems_per_step": nsys, "parallelism": "replicas" if ws > 1 else "single",
-                       "l2": "no flush: each FP64 matrix (%.1f GiB) exceeds L2" % (n * n * 8 / 2 ** 30)},
+            "config": bench_config(args, nsys, ws),
             "roofline": roof,
             "roofline_other_kernels": others,
             "cpu_baseline": cpu,
