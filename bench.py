@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=16384)
+    ap.add_argument("--n", "--matrix-size", dest="n", type=int, default=16384)
     ap.add_argument("--prec", default="fp16x3")
     ap.add_argument("--nb", type=int, default=256)
     ap.add_argument("--restart", type=int, default=50)
