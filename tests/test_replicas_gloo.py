@@ -37,7 +37,7 @@ def _worker(rank, port, out):
 @pytest.mark.skipif(torch.cuda.is_available(), reason="the gloo path is the CPU one")
 def test_max_over_ranks_and_barrier():
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_worker, args=(port, out), nprocs=2, join=True)
         assert dict(out) == {0: 11.0, 1: 11.0}
