@@ -98,19 +98,39 @@ def lowprec_product(L21, U12, prec):
     raise ValueError(prec)
 
 
-def lu_lowprec(A, nb, prec):
+def lu_lowprec(A, nb, prec, with_gap=False, force_ipiv=None):
     """Blocked right-looking GEPP of fp32(A). Returns (W packed L\\U as FP32 values in float64,
-    ipiv int32 1-based, info)."""
+    ipiv int32 1-based, info), and with with_gap=True also the smallest relative
+    gap (|a_p| - |a_second|) / |a_p| between the two largest candidates of any
+    pivot search (1.0 when no column has two candidates) -- the diagnostic that
+    tells whether a second elimination with slightly different rounding must
+    choose the same pivots.
+
+    force_ipiv (1-based, as returned): take these pivots instead of searching
+    (another implementation's choices); the extra return value is then the
+    largest relative shortfall (max|a| - |a_forced|) / max|a| of a forced pivot
+    against the column's largest candidate (0.0 when every forced pivot is a
+    largest candidate)."""
     W = to_fp32(np.array(A, dtype=np.float64, order="F"))
     n = W.shape[0]
     ipiv = np.zeros(n, dtype=np.int32)
     info = 0
+    gap = 1.0
+    slack = 0.0
     for k0 in range(0, n, nb):
         k1 = min(k0 + nb, n)
         # 1. panel, unblocked, FP64 arithmetic rounded to FP32
         for j in range(k0, k1):
             col = np.abs(W[j:, j])
-            p = j + int(np.argmax(col))          # first maximum -> lowest index
+            if force_ipiv is not None:
+                p = int(force_ipiv[j]) - 1
+                if col.max() > 0:
+                    slack = max(slack, float((col.max() - col[p - j]) / col.max()))
+            else:
+                p = j + int(np.argmax(col))          # first maximum -> lowest index
+            if col.shape[0] > 1 and col.max() > 0:
+                top2 = np.sort(col)[-2:]
+                gap = min(gap, float((top2[1] - top2[0]) / top2[1]))
             ipiv[j] = p + 1
             if W[p, j] != 0.0:
                 if p != j:
@@ -130,6 +150,10 @@ def lu_lowprec(A, nb, prec):
         # 3. trailing update in the update precision
         D = lowprec_product(W[k1:, k0:k1], W[k0:k1, k1:], prec)
         W[k1:, k1:] = (W[k1:, k1:].astype(np.float32) - D.astype(np.float32)).astype(np.float64)
+    if force_ipiv is not None:
+        return W, ipiv, info, slack
+    if with_gap:
+        return W, ipiv, info, gap
     return W, ipiv, info
 
 

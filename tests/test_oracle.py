@@ -295,3 +295,90 @@ def test_grad_central_differences():
         Am = A.copy(order="F"); Am[i, j] -= h
         fd = (f(Ap) - f(Am)) / (2 * h)
         assert abs(fd - gA[i, j]) <= 1e-6 * max(1.0, abs(gA[i, j]))
+
+
+# ------------------------------------------------- pivot-gap diagnostic (C11)
+# The diagnostic decides whether pivot vectors are compared at all, so it is
+# pinned on hand-built matrices whose gaps are known exactly (dyadic entries:
+# every step below is exact in FP64).
+def test_min_pivot_gap_known_column():
+    # column 0: |-1| wins over |0.75| -> gap (1 - 0.75) / 1 = 1/4; the 2 x 2
+    # remainder has an obvious winner chosen so that its gap is larger
+    A = np.array([[0.5, 0.0, 0.0], [-1.0, 1.0, 0.0], [0.75, 0.0, 1.0]], order="F")
+    # after step 0 (rows 0 and 1 swapped, l = (-0.5, -0.75)): column 1 rows 1, 2
+    # hold 0 + 0.5 * 1 = 0.5 and 0 + 0.75 * 1 = 0.75 -> gap (0.75 - 0.5) / 0.75 = 1/3
+    assert oracle.min_pivot_gap(A) == 0.25
+
+
+def test_min_pivot_gap_exact_tie():
+    A = np.array([[1.0, 2.0], [-1.0, 3.0]], order="F")
+    assert oracle.min_pivot_gap(A) == 0.0
+
+
+def test_min_pivot_gap_single_candidate():
+    assert oracle.min_pivot_gap(np.array([[3.0]], order="F")) == 1.0
+    # the last column always has one candidate and never lowers the gap
+    A = np.array([[4.0, 1.0], [1.0, 5.0]], order="F")
+    assert oracle.min_pivot_gap(A) == 0.75
+    assert oracle.min_pivot_gap(np.zeros((0, 0), order="F")) == 1.0
+
+
+@pytest.mark.parametrize("a,b,gap", [(0.375, -0.5, 0.25), (0.5, -0.5, 0.0), (0.25, -0.75, 0.5)])
+def test_min_pivot_gap_after_elimination(a, b, gap):
+    """Column 1 before elimination holds 1, 0.5 + a, 0.5 + b (no tie among rows
+    1 and 2 when a = 0.5, b = -0.5: 1.0 and 0.0); after step 0 (pivot 2, gap
+    1/2, multipliers 1/2) rows 1 and 2 of column 1 hold a and b, so the gap of
+    step 1 is (max - min) / max of |a|, |b|. The diagnostic must see the
+    eliminated values, not the raw ones."""
+    A = np.array([[2.0, 1.0, 0.0], [1.0, 0.5 + a, 0.0], [1.0, 0.5 + b, 1.0]], order="F")
+    assert oracle.min_pivot_gap(A) == gap
+    # only the steps asked for count: step 0 alone has gap 1/2
+    assert oracle.min_pivot_gap(A, 1) == 0.5
+
+
+# ---------------------------------------- k elimination steps (ksteps < n)
+@pytest.mark.parametrize("n,k", [(33, 1), (33, 3), (33, 16), (64, 63)])
+def test_getrf_steps_block_identity(n, k):
+    """After k steps of GEPP on A, with P the first k interchanges, the array
+    holds L11\\U11, U12, the multipliers L21 and the Schur complement S such
+    that P A = [L11 0; L21 I] [U11 U12; 0 S]. Dyadic inputs: every product and
+    sum below is exact, so the identity holds bit for bit; the first k pivots
+    are those of the full factorisation and of LAPACK."""
+    A, _, _, _ = inputs.dyadic_lu(n, seed=700 + n + k)
+    An = _np(A)
+    W, ipiv, info = oracle.getrf(An, ksteps=k)
+    assert info == 0
+    P = np.arange(n)
+    for j in range(k):
+        p = ipiv[j] - 1
+        P[j], P[p] = P[p], P[j]
+    B = An[P]
+    L11 = np.tril(W[:k, :k], -1) + np.eye(k)
+    U11 = np.triu(W[:k, :k])
+    U12 = W[:k, k:]
+    L21 = W[k:, :k]
+    S = W[k:, k:]
+    assert np.array_equal(L11 @ U11, B[:k, :k])
+    assert np.array_equal(L11 @ U12, B[:k, k:])
+    assert np.array_equal(L21 @ U11, B[k:, :k])
+    assert np.array_equal(L21 @ U12 + S, B[k:, k:])
+    _, ipiv_full, _ = oracle.getrf(An)
+    assert np.array_equal(ipiv[:k], ipiv_full[:k])
+    _, piv_lapack = torch.linalg.lu_factor(A)
+    assert np.array_equal(ipiv[:k], piv_lapack.numpy()[:k])
+
+
+def test_getrf_steps_schur_complement_random():
+    """Random input: the trailing block after k steps is the Schur complement
+    B22 - B21 B11^{-1} B12 of the permuted matrix (numpy solve as the library
+    step), to within the rounding of k elimination steps."""
+    n, k = 120, 40
+    An = _np(inputs.uniform(n, seed=77))
+    W, ipiv, _ = oracle.getrf(An, ksteps=k)
+    P = np.arange(n)
+    for j in range(k):
+        p = ipiv[j] - 1
+        P[j], P[p] = P[p], P[j]
+    B = An[P]
+    S = B[k:, k:] - B[k:, :k] @ np.linalg.solve(B[:k, :k], B[:k, k:])
+    assert np.abs(W[k:, k:] - S).max() <= 1e-12 * max(1.0, np.abs(S).max())

@@ -142,3 +142,45 @@ def test_split_product_accuracy():
            for p in ("fp16", "fp16x3", "bf16", "bf16x3", "fp32")}
     assert err["fp16x3"] <= 2.0 ** -20 and err["fp16x3"] < err["fp16"] / 50
     assert err["bf16x3"] <= 2.0 ** -15 and err["bf16x3"] < err["bf16"] / 50
+
+
+# ------------------------------- pivot-gap diagnostic of the low-precision LU
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16", "fp16", "fp16x3", "bf16x3"])
+@pytest.mark.parametrize("a,b,gap", [(0.375, -0.5, 0.25), (0.5, -0.5, 0.0), (0.25, -0.75, 0.5)])
+def test_lowprec_gap_hand_built(prec, a, b, gap):
+    """The 3 x 3 matrices whose gaps are known exactly (step 0: 1/2; step 1:
+    (max - min) / max of |a|, |b|, visible only after elimination). Every value
+    and product here is exact in all six precisions, with nb = 1 (the update
+    between the columns runs in the low precision) and nb = 3 (none)."""
+    A = np.array([[2.0, 1.0, 0.0], [1.0, 0.5 + a, 0.0], [1.0, 0.5 + b, 1.0]])
+    for nb in (1, 3):
+        _, _, _, g = M.lu_lowprec(A, nb, prec, with_gap=True)
+        assert g == gap
+    # a single candidate never lowers it; an exact tie in column 0 gives 0
+    assert M.lu_lowprec(np.array([[5.0]]), 1, prec, with_gap=True)[3] == 1.0
+    assert M.lu_lowprec(np.array([[1.0, 2.0], [-1.0, 3.0]]), 1, prec, with_gap=True)[3] == 0.0
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16x3"])
+@pytest.mark.parametrize("n,nb", [(37, 8), (96, 32)])
+def test_lowprec_forced_pivots(prec, n, nb):
+    """Forced pivots: the generator's own row order on an exact dyadic product
+    recovers L and U bit for bit with no shortfall; the oracle's own pivots
+    reproduce its free run exactly."""
+    A, L0, U0, perm = inputs.dyadic_lu(n, seed=800 + n)
+    W, ipiv, info = M.lu_lowprec(A.numpy(), nb, prec)
+    Wf, ipf, infof, slack = M.lu_lowprec(A.numpy(), nb, prec, force_ipiv=ipiv)
+    assert np.array_equal(Wf, W) and np.array_equal(ipf, ipiv) and slack == 0.0
+    # pivots that reproduce P0 without being the searched ones are impossible here
+    # (|l| < 1: every pivot is the strict maximum), so forcing ipiv = the searched
+    # one is the only zero-slack choice; forcing the identity is not
+    _, _, _, s_id = M.lu_lowprec(A.numpy(), nb, prec, force_ipiv=np.arange(1, n + 1))
+    assert (s_id > 0.0) == (not np.array_equal(ipiv, np.arange(1, n + 1)))
+
+
+def test_lowprec_forced_pivot_shortfall_known():
+    """Column 0 holds 0.5, -1, 0.75: forcing row 2 (|0.75|) falls short of the
+    maximum |-1| by exactly 1/4; forcing row 1 by 0."""
+    A = np.array([[0.5, 0.0, 0.0], [-1.0, 1.0, 0.0], [0.75, 0.0, 1.0]])
+    assert M.lu_lowprec(A, 3, "fp32", force_ipiv=[3, 2, 3])[3] == 0.25
+    assert M.lu_lowprec(A, 3, "fp32", force_ipiv=[2, 3, 3])[3] == 0.0
