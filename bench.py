@@ -181,15 +181,17 @@ def gemm_tc_algorithmic_flops(n, nb):
     return tot
 
 
-def panel_algorithmic_bytes(n, elem):
+def panel_algorithmic_bytes(n, elem, nb):
     """Each panel launch reads and writes its slab (32 columns, rows k..n) once, and
-    its interchange CTAs read and write the two rows of each of its (at most 32)
-    interchanges in every other column of the matrix."""
+    reads and writes the two rows of each of its (at most 32) interchanges in the
+    other columns of its outer block (nb - 32 of them)."""
     tot = 0.0
     for j0 in range(0, n, 32):
         w = min(32, n - j0)
+        k0 = (j0 // nb) * nb
+        others = min(nb, n - k0) - w
         tot += 2.0 * (n - j0) * w * elem
-        tot += 2.0 * 2.0 * w * (n - w) * elem
+        tot += 2.0 * 2.0 * w * others * elem
     return tot
 
 
@@ -394,11 +396,12 @@ def run_ours(args, ws, rank):
         peak, bound, unit = None, "alu", "TFLOP/s"
         per_launch_units = "2*M*N*K"
     elif dominant == "panel":
-        alg = panel_algorithmic_bytes(n, 4) * nsys * steps_seen
+        alg = panel_algorithmic_bytes(n, 4, args.nb) * nsys * steps_seen
         achieved = alg / (dom_ms * 1e-3) / 1e9
         peak, bound, unit = pk.get("hbm_gbs"), "hbm", "GB/s"
         per_launch_units = ("panel slab read + written once (32 columns x rows, FP32) + the two rows of "
-                            "each of its 32 interchanges read + written in the other n - 32 columns")
+                            "each of its 32 interchanges read + written in the other nb - 32 columns "
+                            "of its outer block")
     elif dominant == "trsv":
         alg = trsv_algorithmic_bytes(n, 4) * dom_count
         achieved = alg / (dom_ms * 1e-3) / 1e9
@@ -413,14 +416,16 @@ def run_ours(args, ws, rank):
     if per_kind.get("gemm_tc", (0, 0.0))[1] > 0:
         alg_tc = gemm_tc_algorithmic_flops(n, args.nb) * nsys
         mult = 3 if args.prec in ("fp16x3", "bf16x3") else 1
-        ach = alg_tc * mult / (per_kind["gemm_tc"][1] * 1e-3) / 1e12
-        pk_tc = pk.get("bf16_tflops")
+        ach = alg_tc / (per_kind["gemm_tc"][1] * 1e-3) / 1e12
+        pk_tc = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
         if args.prec == "tf32" and pk_tc:
             pk_tc = pk_tc / 2.0
         others.append({"kernel": "gemm_tc", "bound": "tensor", "achieved": ach, "peak": pk_tc,
                        "unit": "TFLOP/s", "frac": ach / pk_tc if pk_tc else None,
-                       "algorithmic_units": "2*M*N*K per rank-nb update, x%d for the split operands "
-                                            "(executed on the tensor pipe)" % mult})
+                       "peak_kind": "sustained (the update runs inside a long step)",
+                       "executed_on_tensor_pipe_tflops": ach * mult,
+                       "algorithmic_units": "2*M*N*K of the method per rank-nb update (the split "
+                                            "operands execute it %dx on the tensor pipe)" % mult})
     if per_kind.get("trsv", (0, 0.0))[1] > 0:
         cnt, ms_tr = per_kind["trsv"]
         ach = trsv_algorithmic_bytes(n, 4) * cnt / (ms_tr * 1e-3) / 1e9

@@ -76,8 +76,8 @@ const char *gbla_last_error(void);
  * gbla_launch_count: kernels this library has launched in this process.
  * gbla_prof_enable(mask): bracket every later launch group of the kinds set
  *   in mask (bit k = kind k) with a pair of CUDA events on its stream.
- *   Kinds: 0 panel, 1 laswp (records nothing: row interchanges run inside
- *   the panel launches), 2 trsm, 3 gemm_simt, 4 gemm_tc, 5 convert,
+ *   Kinds: 0 panel, 1 laswp (an outer block's row interchanges on the
+ *   columns outside it), 2 trsm, 3 gemm_simt, 4 gemm_tc, 5 convert,
  *   6 trsv, 7 matvec, 8 mgs, 9 gmres_update, 10 permute, 11 copy, 12 batched.
  * gbla_prof_read: number of recorded groups of `kind` and their summed
  *   device time in ms (waits for the events). gbla_prof_reset forgets them.
@@ -99,12 +99,14 @@ uint64_t gbla_get_wait_timeout_ns(void);
 
 /* ------------------------------------------------------------------------
  * FP64 LU with partial pivoting (paper section 2; steps a1-a4).
- * Blocked right-looking: for each block column of width nb the panel is
- * factored by a cooperative kernel (warp-shuffle argmax pivot search, row
- * swaps and scaling on a shared-memory-resident slab, one grid barrier per
- * column), the interchanges are applied to the other columns, the U row
- * block is solved against the unit lower diagonal block, and the trailing
- * matrix receives one rank-nb update.
+ * Blocked right-looking: each block column of width nb is factored as
+ * 32-column panels (warp-shuffle argmax pivot search, row swaps, scaling and
+ * rank-1 updates on register-resident rows of one thread-block cluster, or of
+ * cooperative CTAs for panels taller than a cluster holds), each followed by
+ * the solve and update of the rest of the block column; then the block
+ * column's row interchanges are applied to every other column, the U row
+ * block is solved against the unit lower diagonal block and the trailing
+ * matrix receives one rank-nb update. All work is ordered on `stream`.
  *   n      order of A (n >= 0)
  *   A      n x n, overwritten by L (strict lower, unit diagonal implied) and U
  *   lda    leading dimension (>= max(1, n))
@@ -122,14 +124,16 @@ int gbla_lu_factor(int n, double *A, int lda, int *ipiv, int *d_info, int nb,
  * host application that owns every device allocation, or a path that must
  * never reach the allocator). The paper has no counterpart; it computes the
  * same factorisation, with the same kernels, as gbla_lu_factor.
- *   Its only scratch, the panel kernel's exchange slots, is a fixed array of
- *   about 290 KiB inside the library's device image (room for devices with up
- *   to 256 multiprocessors; a device with more returns GBLA_ERR_WORKSPACE).
- *   Every GPU that loads the library holds that array until the process
- *   exits. The call itself allocates nothing.
+ *   Its only scratch, the panel kernels' exchange slots, is a fixed array of
+ *   about 290 KiB inside the library's device image (room for the 256 CTAs
+ *   that the panel kernels use at most, on any device). Every GPU that loads
+ *   the library holds that array until the process exits. The call itself
+ *   allocates nothing: all of its work runs on `stream`.
  *   The first call on a device looks up the array's device address for that
- *   device (cudaGetSymbolAddress, with the device current); make that first
- *   call before any stream capture.
+ *   device (cudaGetSymbolAddress, with the device current) and keeps it; make
+ *   that first call before any stream capture. The kept address belongs to
+ *   the device's current context: after cudaDeviceReset the process must not
+ *   call this entry point again.
  *   All calls share the one array and it keeps the last call's contents
  *   (each call clears it before use): calls whose work overlaps on the GPU --
  *   on different streams, or from different host threads -- race with each
@@ -183,12 +187,15 @@ int gbla_lu_factor_mixed(int n, const double *A, int lda, float *F, int ldf, int
                          gbla_stream_t stream);
 
 /* ------------------------------------------------------------------------
- * GMRES-based iterative refinement (step a7-a8) for one right-hand side:
- * x0 = M^{-1} b with M = P^t L U from gbla_lu_factor_mixed (FP32 factors,
- * FP64 arithmetic); then repeat r = b - A x (FP64), stop when
- * ||r||_inf / (||A||_inf ||x||_inf) <= tol; otherwise run GMRES(m) (modified
- * Gram-Schmidt, Givens rotations) on M^{-1} A d = M^{-1} r from d = 0 until
- * the least-squares residual falls below inner_tol * ||M^{-1} r||_2, and set
+ * GMRES-based iterative refinement (steps a7-a8; the GMRES of paper section
+ * 2 with Gram-Schmidt orthogonalisation and restarts): x0 = M^{-1} b with
+ * M = P^t L U from gbla_lu_factor_mixed (FP32 factors, FP64 arithmetic);
+ * then repeat r = b - A x (FP64), stop when
+ * ||r||_inf / (||A||_inf ||x||_inf) <= tol; otherwise run restarted GMRES(m)
+ * (modified Gram-Schmidt, Givens rotations) on M^{-1} A d = z, z = M^{-1} r,
+ * from d = 0: up to `restarts` cycles of at most m steps, cycle c > 0
+ * starting from the current d with the residual z - M^{-1} A d, until the
+ * least-squares residual falls below inner_tol * ||z||_2; then
  * x <- x + d (FP64).
  * SYNCHRONOUS: reads one scalar back per inner step and per outer step
  * (it synchronises `stream`). Host pointers: opts, stats.
@@ -199,7 +206,8 @@ typedef struct {
   double tol;       /* normwise backward-error target, e.g. 1e-14 */
   double inner_tol; /* GMRES relative tolerance, e.g. 1e-8 */
   int max_outer;    /* refinement steps, e.g. 10 */
-  int restart_m;    /* GMRES Krylov dimension per call, 1..128, e.g. 50 */
+  int restart_m;    /* GMRES Krylov dimension per cycle, 1..128, e.g. 50 */
+  int restarts;     /* GMRES cycles per refinement step (0 or 1: one cycle) */
 } gbla_gmresir_opts;
 
 typedef struct {
@@ -215,6 +223,18 @@ int gbla_gmresir_solve(int n, const double *A, int lda, const float *F, int ldf,
                        const int *ipiv, const double *b, double *x,
                        const gbla_gmresir_opts *opts, gbla_gmresir_stats *stats,
                        void *d_work, size_t work_bytes, gbla_stream_t stream);
+
+/* The same refinement for nrhs right-hand sides (B, X: n x nrhs, ldb, ldx),
+ * sharing one set-up of the factors (pivot permutation, inverted diagonal
+ * blocks) and one workspace (gbla_gmresir_workspace(n, restart_m)); each
+ * column is refined on its own, with its own entry of stats[0 .. nrhs).
+ * Returns 0 when every column converged, GBLA_ERR_NOT_CONVERGED when one or
+ * more did not (see stats[k].converged), GBLA_ERR_TIMEOUT on a wait that gave
+ * up. Synchronous, like gbla_gmresir_solve. */
+int gbla_gmresir_solve_nrhs(int n, int nrhs, const double *A, int lda, const float *F, int ldf,
+                            const int *ipiv, const double *B, int ldb, double *X, int ldx,
+                            const gbla_gmresir_opts *opts, gbla_gmresir_stats *stats,
+                            void *d_work, size_t work_bytes, gbla_stream_t stream);
 
 /* ------------------------------------------------------------------------
  * Batched LU with partial pivoting + solve (step a9: the factorisation and

@@ -24,7 +24,8 @@ _d = ctypes.c_double
 
 
 class GmresirOpts(ctypes.Structure):
-    _fields_ = [("tol", _d), ("inner_tol", _d), ("max_outer", _i), ("restart_m", _i)]
+    _fields_ = [("tol", _d), ("inner_tol", _d), ("max_outer", _i), ("restart_m", _i),
+                ("restarts", _i)]
 
 
 class GmresirStats(ctypes.Structure):
@@ -55,6 +56,9 @@ _SIGS = {
     "gbla_gmresir_workspace": ([_i, _i], _sz),
     "gbla_gmresir_solve": ([_i, _vp, _i, _vp, _i, _vp, _vp, _vp, ctypes.POINTER(GmresirOpts),
                             ctypes.POINTER(GmresirStats), _vp, _sz, _vp], _i),
+    "gbla_gmresir_solve_nrhs": ([_i, _i, _vp, _i, _vp, _i, _vp, _vp, _i, _vp, _i,
+                                 ctypes.POINTER(GmresirOpts), ctypes.POINTER(GmresirStats), _vp, _sz,
+                                 _vp], _i),
     "gbla_lu_batched_workspace": ([_i], _sz),
     "gbla_lu_solve_batched": ([_i] + [_vp] * 9 + [_i, _i, _i, _vp, _sz, _vp], _i),
     "gbla_lu_solve_batched_f32": ([_i] + [_vp] * 9 + [_i, _i, _i, _vp, _sz, _vp], _i),

@@ -152,26 +152,43 @@ def lu_factor_mixed(A, prec="bf16", nb=256, F=None):
     return F, ipiv[:n], info
 
 
-def gmresir(A, F, ipiv, b, tol=1e-14, inner_tol=1e-8, max_outer=10, restart_m=50, x=None):
+def _stats_dict(st):
+    return {"outer": st.outer, "inner": st.inner, "converged": bool(st.converged),
+            "beta": st.beta, "beta0": st.beta0}
+
+
+def gmresir(A, F, ipiv, b, tol=1e-14, inner_tol=1e-8, max_outer=10, restart_m=50, restarts=1,
+            x=None):
     """GMRES-based refinement of A x = b with the mixed factors. Synchronous.
-    Returns (x, stats dict); raises GblaError on a hard failure, not on non-convergence."""
+    b: a vector (returns x, stats dict) or an n x k matrix (every column refined
+    on its own, one set-up of the factors; returns X n x k, list of k dicts).
+    Raises GblaError on a hard failure, not on non-convergence."""
     _require_cuda(A, F, ipiv, b)
     L = _lib.load()
     n = A.shape[0]
     Ac = colmajor(A, torch.float64)
     Fc = colmajor(F, torch.float32)
+    opts = _lib.GmresirOpts(tol, inner_tol, max_outer, restart_m, restarts)
+    ws = _ws(L.gbla_gmresir_workspace(n, restart_m), A.device)
+    if b.dim() == 2:
+        Bc = colmajor(b, torch.float64)
+        k = Bc.shape[1]
+        X = torch.empty_strided((n, k), (1, max(1, n)), dtype=torch.float64, device=A.device)
+        st = (_lib.GmresirStats * max(k, 1))()
+        rc = L.gbla_gmresir_solve_nrhs(n, k, _p(Ac), _ld(Ac), _p(Fc), _ld(Fc), _p(ipiv), _p(Bc), _ld(Bc),
+                                       _p(X), _ld(X), ctypes.byref(opts), st, _p(ws), ws.numel(),
+                                       _stream())
+        if rc not in (0, _lib.GBLA_ERR_NOT_CONVERGED):
+            raise GblaError("gbla_gmresir_solve_nrhs", rc)
+        return X, [_stats_dict(st[j]) for j in range(k)]
     bc = b.reshape(-1).to(torch.float64).contiguous()
     x = torch.empty(max(n, 1), dtype=torch.float64, device=A.device) if x is None else x
-    opts = _lib.GmresirOpts(tol, inner_tol, max_outer, restart_m)
     st = _lib.GmresirStats()
-    ws = _ws(L.gbla_gmresir_workspace(n, restart_m), A.device)
     rc = L.gbla_gmresir_solve(n, _p(Ac), _ld(Ac), _p(Fc), _ld(Fc), _p(ipiv), _p(bc), _p(x),
                               ctypes.byref(opts), ctypes.byref(st), _p(ws), ws.numel(), _stream())
     if rc not in (0, _lib.GBLA_ERR_NOT_CONVERGED):
         raise GblaError("gbla_gmresir_solve", rc)
-    stats = {"outer": st.outer, "inner": st.inner, "converged": bool(st.converged),
-             "beta": st.beta, "beta0": st.beta0}
-    return x[:n], stats
+    return x[:n], _stats_dict(st)
 
 
 def solve_mixed(A, b, prec="bf16", nb=256, **kw):
@@ -179,16 +196,10 @@ def solve_mixed(A, b, prec="bf16", nb=256, **kw):
     matrix is factored once and every column is refined on its own: x is n x k and
     stats a list of k dicts."""
     F, ipiv, info = lu_factor_mixed(A, prec, nb)
-    if b.dim() == 2:
-        xs, sts = [], []
-        for j in range(b.shape[1]):
-            x, st = gmresir(A, F, ipiv, b[:, j], **kw)
-            st["info"] = int(info.item())
-            xs.append(x)
-            sts.append(st)
-        return torch.stack(xs, dim=1), sts
     x, st = gmresir(A, F, ipiv, b, **kw)
-    st["info"] = int(info.item())
+    inf = int(info.item())
+    for d in (st if isinstance(st, list) else [st]):
+        d["info"] = inf
     return x, st
 
 

@@ -109,19 +109,23 @@ void prof_end(int kind, cudaStream_t s) {
 static thread_local char g_last_error[256] = "";
 
 static void clear_error() { g_last_error[0] = 0; }
+void api_clear_error() { clear_error(); }
 
+static void record_error_in(cudaError_t e, const char* what, const char* file, int line) {
+  snprintf(g_last_error, sizeof(g_last_error), "%s (%s) at %s:%d: %s", cudaGetErrorName(e), what,
+           file, line, cudaGetErrorString(e));
+}
 static void record_error(cudaError_t e, const char* what, int line) {
-  snprintf(g_last_error, sizeof(g_last_error), "%s (%s) at api.cu:%d: %s", cudaGetErrorName(e), what,
-           line, cudaGetErrorString(e));
+  record_error_in(e, what, "api.cu", line);
 }
 
 // the first failure of a call is kept; the outer wrappers do not overwrite it
-static int cuda_status_at(cudaError_t e, const char* what, int line) {
+int api_cuda_status(cudaError_t e, const char* what, const char* file, int line) {
   if (e == cudaSuccess) return GBLA_OK;
-  if (g_last_error[0] == 0) record_error(e, what, line);
+  if (g_last_error[0] == 0) record_error_in(e, what, file, line);
   return GBLA_ERR_CUDA;
 }
-#define cuda_status(e) cuda_status_at((e), #e, __LINE__)
+#define cuda_status(e) api_cuda_status((e), #e, "api.cu", __LINE__)
 
 #define GBLA_TRYK(kind, stream, expr)      \
   do {                                     \
@@ -147,11 +151,12 @@ static bool aligned256(const void* p) { return (reinterpret_cast<uintptr_t>(p) &
 
 // ----------------------------------------------------------------------------
 // Blocked right-looking LU over a generic storage type. Outer blocks of width
-// nb; inside each, inner panels of width kPanelWidth factored by the
-// cooperative kernel (whose interchange CTAs also apply the panel's row swaps
-// to every other column of the matrix), followed by the inner substitution and
-// update restricted to the outer block (one fused launch). After the outer block: the U row block
-// and the trailing update.
+// nb; inside each, inner panels of width kPanelWidth factored by the panel
+// kernel (which also applies the panel's row interchanges to the other
+// columns of the outer block), followed by the inner substitution and update
+// restricted to the outer block (one fused launch). After the outer block:
+// its interchanges on every other column (one launch), the U row block and
+// the trailing update.
 static size_t lu_work_layout(Carver& c, int n, int nb, int prec, LuWork* w) {
   double* slots = c.take<double>(panel_slots_doubles());
   if (w) {
@@ -182,15 +187,16 @@ template <typename Ts>
 cudaError_t blocked_lu(int n, Ts* A, int lda, int* ipiv, int* info, int nb, int prec,
                               const LuWork& w, cudaStream_t s) {
   typedef Ts Tc_trsm;  // substitution arithmetic: FP64 for FP64 storage, FP32 for FP32
-  unsigned* inner_ctr = reinterpret_cast<unsigned*>(w.slots + kPanelExchangeDoubles + kPanelWidth);
+  unsigned* inner_ctr = reinterpret_cast<unsigned*>(w.slots + kPanelExchangeDoubles);
   cudaError_t e;
   for (int k0 = 0; k0 < n; k0 += nb) {
     const int kb = std::min(nb, n - k0);
     for (int j0 = k0; j0 < k0 + kb; j0 += kPanelWidth) {
       const int jb = std::min(kPanelWidth, k0 + kb - j0);
-      // the panel launch also applies its interchanges to all other columns
+      // the panel launch also applies its interchanges to the rest of the outer block
       PROF(KK_PANEL, s, launch_panel<Ts>(A + j0 + (size_t)j0 * lda, lda, n - j0, jb, j0, ipiv + j0, info,
-                                         w.slots, (unsigned)(j0 / kPanelWidth), n, s));
+                                         w.slots, (unsigned)(j0 / kPanelWidth), j0 - k0,
+                                         k0 + kb - j0 - jb, s));
       if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
       const int nrest = k0 + kb - j0 - jb;
       if (nrest > 0 && jb == kPanelWidth) {
@@ -209,6 +215,10 @@ cudaError_t blocked_lu(int n, Ts* A, int lda, int* ipiv, int* info, int nb, int 
         if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
       }
     }
+    // the block's interchanges on every column outside it (the U row block
+    // and the trailing update below read the interchanged rows)
+    PROF(KK_LASWP, s, launch_laswp_block<Ts>(A, lda, n, n, k0, kb, ipiv + k0, k0, k0 + kb, s));
+    if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
     const int nt = n - k0 - kb;
     if (nt <= 0) continue;
     const bool tensor = prec_is_tensor(prec);
@@ -656,6 +666,8 @@ struct IrWork {
   double* anorm;
   double* beta;
   double* part;
+  double* z;   // M^{-1} r of the current refinement step
+  double* d;   // the correction being built by the restart cycles
 };
 
 static size_t ir_layout(Carver& c, int n, int m, IrWork* w) {
@@ -683,6 +695,8 @@ static size_t ir_layout(Carver& c, int n, int m, IrWork* w) {
   t.anorm = c.take<double>(1);
   t.beta = c.take<double>(1);
   t.part = c.take<double>(residual_work_doubles(nn, 1));
+  t.z = c.take<double>(nn);
+  t.d = c.take<double>(nn);
   if (w) *w = t;
   return c.off;
 }
@@ -718,42 +732,25 @@ static int read_scalar(double* host, const double* dev, const int* d_info, cudaS
   return info == GBLA_INFO_TIMEOUT ? GBLA_ERR_TIMEOUT : GBLA_OK;
 }
 
-int gbla_gmresir_solve(int n, const double* A, int lda, const float* F, int ldf, const int* ipiv,
-                       const double* b, double* x, const gbla_gmresir_opts* opts,
-                       gbla_gmresir_stats* stats, void* d_work, size_t work_bytes,
-                       gbla_stream_t stream) {
-  clear_error();
-  if (n < 0) return -1;
-  if (n > 0 && !A) return -2;
-  if (lda < std::max(1, n)) return -3;
-  if (n > 0 && !F) return -4;
-  if (ldf < std::max(1, n)) return -5;
-  if (n > 0 && !ipiv) return -6;
-  if (n > 0 && !b) return -7;
-  if (n > 0 && !x) return -8;
-  if (!opts || opts->restart_m < 1 || opts->restart_m > 128 || opts->max_outer < 0 ||
-      !(opts->tol >= 0.0) || !(opts->inner_tol >= 0.0))
-    return -9;
-  if (!stats) return -10;
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if (!d_work || !aligned256(d_work)) return GBLA_ERR_WORKSPACE;
+static int check_ir_opts(const gbla_gmresir_opts* o) {
+  return (o && o->restart_m >= 1 && o->restart_m <= 128 && o->max_outer >= 0 && o->restarts >= 0 &&
+          o->tol >= 0.0 && o->inner_tol >= 0.0)
+             ? 0
+             : 1;
+}
+
+// One right-hand side, with the per-call set-up (perm, inverted diagonal
+// blocks, ||A||) already in w. Refinement step: r = b - A x and its backward
+// error; z = M^{-1} r; then up to `restarts` GMRES(m) cycles on
+// M^{-1} A d = z (cycle c > 0 restarts from the current d with the residual
+// z - M^{-1} A d), stopping once the least-squares residual is below
+// inner_tol * ||z||_2; x <- x + d.
+static int gmresir_one(int n, const double* A, int lda, const float* F, int ldf, const double* b,
+                       double* x, const gbla_gmresir_opts* opts, gbla_gmresir_stats* stats,
+                       const IrWork& w, cudaStream_t s) {
   const int m = opts->restart_m;
-  Carver c(d_work, work_bytes);
-  IrWork w;
-  ir_layout(c, n, m, &w);
-  if (!c.ok) return GBLA_ERR_WORKSPACE;
+  const int cycles = std::max(1, opts->restarts);
   memset(stats, 0, sizeof(*stats));
-  if (n == 0) {
-    stats->converged = 1;
-    return GBLA_OK;
-  }
-  const DeviceProps& dp = device_props();
-  if (!dp.coop) return GBLA_ERR_DEVICE;
-  GBLA_TRY(cudaMemsetAsync(w.info, 0, sizeof(int), s));
-  GBLA_TRYK(KK_PERM, s, launch_ipiv_to_perm(n, ipiv, w.perm, s));
-  GBLA_TRYK(KK_TRSV, s, launch_diag_inv<float>(true, true, n, F, ldf, w.DinvL, s));
-  GBLA_TRYK(KK_TRSV, s, launch_diag_inv<float>(false, false, n, F, ldf, w.DinvU, s));
-  GBLA_TRYK(KK_MATVEC, s, launch_row_abs_sum_max(n, A, lda, w.part, w.anorm, s));
   GBLA_TRY(apply_minv(n, F, ldf, w.perm, w.DinvL, w.DinvU, b, x, w.t1, w.t2, w.flags, w.info, s));
   int rc = GBLA_OK;
   for (int outer = 0;; ++outer) {
@@ -770,33 +767,119 @@ int gbla_gmresir_solve(int n, const double* A, int lda, const float* F, int ldf,
       return GBLA_OK;
     }
     if (outer >= opts->max_outer) return GBLA_ERR_NOT_CONVERGED;
-    // z = M^{-1} r, v_0 = z / ||z||
-    GBLA_TRY(apply_minv(n, F, ldf, w.perm, w.DinvL, w.DinvU, w.r, w.w, w.t1, w.t2, w.flags, w.info, s));
-    GBLA_TRYK(KK_MGS, s, launch_mgs_step(n, -1, w.V, w.ldv, w.w, w.H, m + 1, w.cs, w.sn, w.g, w.st, w.slots,
-                             w.counter, w.info, s));
-    double beta_in = 0.0;
-    rc = read_scalar(&beta_in, w.st, w.info, s);
-    if (rc != GBLA_OK) return rc;
-    if (!(beta_in > 0.0)) {
-      stats->converged = 1;
-      return GBLA_OK;
-    }
-    int k = 0;
-    for (int j = 0; j < m; ++j) {
-      // w = M^{-1} A v_j
-      GBLA_TRYK(KK_MATVEC, s, launch_residual(n, 1, A, lda, w.V + (size_t)j * w.ldv, n, nullptr, n, w.w, n, w.part, s));
-      GBLA_TRY(apply_minv(n, F, ldf, w.perm, w.DinvL, w.DinvU, w.w, w.r, w.t1, w.t2, w.flags, w.info, s));
-      GBLA_TRYK(KK_MGS, s, launch_mgs_step(n, j, w.V, w.ldv, w.r, w.H, m + 1, w.cs, w.sn, w.g, w.st, w.slots,
+    // z = M^{-1} r; d = 0
+    GBLA_TRY(apply_minv(n, F, ldf, w.perm, w.DinvL, w.DinvU, w.r, w.z, w.t1, w.t2, w.flags, w.info, s));
+    GBLA_TRY(cudaMemsetAsync(w.d, 0, sizeof(double) * (size_t)n, s));
+    double znorm = 0.0;
+    for (int cyc = 0; cyc < cycles; ++cyc) {
+      // v_0 = c / ||c|| with c = z (first cycle) or z - M^{-1} A d
+      const double* c0 = w.z;
+      if (cyc > 0) {
+        GBLA_TRYK(KK_MATVEC, s, launch_residual(n, 1, A, lda, w.d, n, nullptr, n, w.w, n, w.part, s));
+        GBLA_TRY(apply_minv(n, F, ldf, w.perm, w.DinvL, w.DinvU, w.w, w.r, w.t1, w.t2, w.flags, w.info, s));
+        GBLA_TRYK(KK_UPDATE, s, launch_axpby(n, 1.0, w.z, -1.0, w.r, w.w, s));
+        c0 = w.w;
+      }
+      GBLA_TRYK(KK_MGS, s, launch_mgs_step(n, -1, w.V, w.ldv, c0, w.H, m + 1, w.cs, w.sn, w.g, w.st, w.slots,
                                w.counter, w.info, s));
-      double res = 0.0;
-      rc = read_scalar(&res, w.st, w.info, s);
+      double beta_in = 0.0;
+      rc = read_scalar(&beta_in, w.st, w.info, s);
       if (rc != GBLA_OK) return rc;
-      k = j + 1;
-      if (res <= opts->inner_tol * beta_in) break;
+      if (cyc == 0) znorm = beta_in;
+      if (!(beta_in > opts->inner_tol * znorm) || !(beta_in > 0.0)) break;
+      int k = 0;
+      double res = beta_in;
+      for (int j = 0; j < m; ++j) {
+        // w = M^{-1} A v_j
+        GBLA_TRYK(KK_MATVEC, s, launch_residual(n, 1, A, lda, w.V + (size_t)j * w.ldv, n, nullptr, n, w.w, n, w.part, s));
+        GBLA_TRY(apply_minv(n, F, ldf, w.perm, w.DinvL, w.DinvU, w.w, w.r, w.t1, w.t2, w.flags, w.info, s));
+        GBLA_TRYK(KK_MGS, s, launch_mgs_step(n, j, w.V, w.ldv, w.r, w.H, m + 1, w.cs, w.sn, w.g, w.st, w.slots,
+                                 w.counter, w.info, s));
+        rc = read_scalar(&res, w.st, w.info, s);
+        if (rc != GBLA_OK) return rc;
+        k = j + 1;
+        if (res <= opts->inner_tol * znorm) break;
+      }
+      stats->inner += k;
+      GBLA_TRYK(KK_UPDATE, s, launch_gmres_update(n, k, w.V, w.ldv, w.H, m + 1, w.g, w.d, s));
+      if (res <= opts->inner_tol * znorm) break;
     }
-    stats->inner += k;
-    GBLA_TRYK(KK_UPDATE, s, launch_gmres_update(n, k, w.V, w.ldv, w.H, m + 1, w.g, x, s));
+    GBLA_TRYK(KK_UPDATE, s, launch_axpby(n, 1.0, w.d, 1.0, x, x, s));
   }
+}
+
+// Per-call set-up of the refinement: the permutation of the pivots, the
+// inverted diagonal blocks of L and U, ||A||_inf.
+static int gmresir_setup(int n, const double* A, int lda, const float* F, int ldf, const int* ipiv,
+                         const IrWork& w, cudaStream_t s) {
+  GBLA_TRY(cudaMemsetAsync(w.info, 0, sizeof(int), s));
+  GBLA_TRYK(KK_PERM, s, launch_ipiv_to_perm(n, ipiv, w.perm, s));
+  GBLA_TRYK(KK_TRSV, s, launch_diag_inv<float>(true, true, n, F, ldf, w.DinvL, s));
+  GBLA_TRYK(KK_TRSV, s, launch_diag_inv<float>(false, false, n, F, ldf, w.DinvU, s));
+  GBLA_TRYK(KK_MATVEC, s, launch_row_abs_sum_max(n, A, lda, w.part, w.anorm, s));
+  return GBLA_OK;
+}
+
+int gbla_gmresir_solve_nrhs(int n, int nrhs, const double* A, int lda, const float* F, int ldf,
+                            const int* ipiv, const double* B, int ldb, double* X, int ldx,
+                            const gbla_gmresir_opts* opts, gbla_gmresir_stats* stats,
+                            void* d_work, size_t work_bytes, gbla_stream_t stream) {
+  clear_error();
+  if (n < 0) return -1;
+  if (nrhs < 0) return -2;
+  if (n > 0 && !A) return -3;
+  if (lda < std::max(1, n)) return -4;
+  if (n > 0 && !F) return -5;
+  if (ldf < std::max(1, n)) return -6;
+  if (n > 0 && !ipiv) return -7;
+  if (n > 0 && nrhs > 0 && !B) return -8;
+  if (ldb < std::max(1, n)) return -9;
+  if (n > 0 && nrhs > 0 && !X) return -10;
+  if (ldx < std::max(1, n)) return -11;
+  if (check_ir_opts(opts)) return -12;
+  if (nrhs > 0 && !stats) return -13;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!d_work || !aligned256(d_work)) return GBLA_ERR_WORKSPACE;
+  Carver c(d_work, work_bytes);
+  IrWork w;
+  ir_layout(c, n, opts->restart_m, &w);
+  if (!c.ok) return GBLA_ERR_WORKSPACE;
+  for (int k = 0; k < nrhs; ++k) memset(&stats[k], 0, sizeof(stats[k]));
+  if (n == 0) {
+    for (int k = 0; k < nrhs; ++k) stats[k].converged = 1;
+    return GBLA_OK;
+  }
+  if (nrhs == 0) return GBLA_OK;
+  const DeviceProps& dp = device_props();
+  if (!dp.coop) return GBLA_ERR_DEVICE;
+  int rc = gmresir_setup(n, A, lda, F, ldf, ipiv, w, s);
+  if (rc != GBLA_OK) return rc;
+  int all = GBLA_OK;
+  for (int k = 0; k < nrhs; ++k) {
+    rc = gmresir_one(n, A, lda, F, ldf, B + (size_t)k * ldb, X + (size_t)k * ldx, opts, &stats[k], w, s);
+    if (rc == GBLA_ERR_NOT_CONVERGED) all = rc;
+    else if (rc != GBLA_OK) return rc;
+  }
+  return all;
+}
+
+int gbla_gmresir_solve(int n, const double* A, int lda, const float* F, int ldf, const int* ipiv,
+                       const double* b, double* x, const gbla_gmresir_opts* opts,
+                       gbla_gmresir_stats* stats, void* d_work, size_t work_bytes,
+                       gbla_stream_t stream) {
+  clear_error();
+  if (n < 0) return -1;
+  if (n > 0 && !A) return -2;
+  if (lda < std::max(1, n)) return -3;
+  if (n > 0 && !F) return -4;
+  if (ldf < std::max(1, n)) return -5;
+  if (n > 0 && !ipiv) return -6;
+  if (n > 0 && !b) return -7;
+  if (n > 0 && !x) return -8;
+  if (check_ir_opts(opts)) return -9;
+  if (!stats) return -10;
+  return gbla_gmresir_solve_nrhs(n, 1, A, lda, F, ldf, ipiv, b, std::max(1, n), x, std::max(1, n),
+                                 opts, stats, d_work, work_bytes, stream);
 }
 
 }  // extern "C"

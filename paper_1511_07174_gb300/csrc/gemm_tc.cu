@@ -45,7 +45,21 @@ GBLA_DEVINL bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
+GBLA_DEVINL bool mbar_test_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait; a limit of 0 does not wait at all (one non-blocking test):
+// try_wait may suspend the thread for a while before it answers.
 GBLA_DEVINL bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+  if (limit_ns == 0) return mbar_test_wait(bar, parity);
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = gbla_now_ns();
   while (!mbar_try_wait(bar, parity)) {
@@ -133,6 +147,10 @@ constexpr int kPsStages = 4;
 constexpr int kPsThreads = 320;  // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
 constexpr int kPsStageC = 32 * 64 * 4;  // one epilogue warp's 32 rows x 64 columns of FP32
 constexpr int kPsSmemBytes = 2 * kPsStages * kTcStageBytes + 8 * kPsStageC + 1024 + 512;
+// Waits for copies and MMAs that have already been issued (leaving the kernel
+// after a failed wait) end when the hardware finishes them; a caller's tiny
+// wait limit must not cut them short.
+constexpr uint64_t kPsDrainFloorNs = 200000000ull;
 
 // Epilogue through the TMA unit: the scaled, negated accumulator is staged in
 // shared memory and added to C by a bulk tensor reduction (C += -D), so the
@@ -183,7 +201,8 @@ __global__ void __launch_bounds__(kPsThreads, 1)
   const uint32_t bar_empty = bar_full + 8 * kPsStages;
   const uint32_t bar_tfull = bar_full + 16 * kPsStages;
   const uint32_t bar_tempty = bar_tfull + 16;
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * kPsStages + 4);
+  const uint32_t bar_drain = bar_tempty + 16;  // the MMA issuer's last commit
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * kPsStages + 5);
   volatile int* s_fail = reinterpret_cast<volatile int*>(tmem_holder + 1);
   volatile int* s_issued = s_fail + 1;
 
@@ -204,6 +223,7 @@ __global__ void __launch_bounds__(kPsThreads, 1)
       mbar_init(bar_tfull + 8 * b, 1);
       mbar_init(bar_tempty + 8 * b, 8);
     }
+    mbar_init(bar_drain, 1);
     *s_fail = 0;
     *s_issued = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -273,6 +293,11 @@ __global__ void __launch_bounds__(kPsThreads, 1)
         }
         mma_commit(bar_tfull + 8 * b);
       }
+      // every MMA this thread issued has finished before tensor memory is freed
+      // (after a failed wait some may still be running)
+      mma_commit(bar_drain);
+      const uint64_t dns = args.wait_ns > kPsDrainFloorNs ? args.wait_ns : kPsDrainFloorNs;
+      if (!mbar_wait_bounded(bar_drain, 0u, dns)) *s_fail = 1;
     }
   } else {  // epilogue warps 2..9: TMEM lane group warp % 4, column half (warp - 2) / 4
     const int eg = warp & 3;
@@ -355,9 +380,9 @@ __global__ void __launch_bounds__(kPsThreads, 1)
     if (threadIdx.x == 0) {
       gbla_flag_timeout(args.info);
       const int issued = *s_issued;
+      const uint64_t dns = args.wait_ns > kPsDrainFloorNs ? args.wait_ns : kPsDrainFloorNs;
       for (int it = (issued > kPsStages ? issued - kPsStages : 0); it < issued; ++it)
-        mbar_wait_bounded(bar_full + 8 * (it % kPsStages), (uint32_t)((it / kPsStages) & 1),
-                          args.wait_ns);
+        mbar_wait_bounded(bar_full + 8 * (it % kPsStages), (uint32_t)((it / kPsStages) & 1), dns);
     }
     __syncthreads();
   }

@@ -52,6 +52,12 @@ struct Carver {
   }
 };
 
+// ---- last-error record of the C entry points (thread-local) ------------------
+void api_clear_error();
+// GBLA_OK for cudaSuccess; otherwise records the first failure of the call
+// (the expression text and line) and returns GBLA_ERR_CUDA.
+int api_cuda_status(cudaError_t e, const char* what, const char* file, int line);
+
 // ---- instrumentation -----------------------------------------------------------
 // Kernel groups that can be bracketed with CUDA events (gbla_prof_*).
 enum KernelKind {
@@ -85,26 +91,37 @@ inline int prec_mma_kind(int p) {
 inline int prec_kmult(int p) { return prec_is_split(p) ? 3 : 1; }
 
 // ---- kernel launchers (all stream-ordered; return cudaError_t) -------------
-constexpr int kPanelWidth = 32;  // inner panel width handled by the cooperative kernel
+constexpr int kPanelWidth = 32;  // inner panel width handled by the panel kernels
 constexpr int kPanelSlotW = 72;  // doubles per published candidate slot
+// The L2-exchange panel kernels use at most kPanelMaxSms CTAs.
+constexpr int kPanelMaxSms = 256;
 // Layout of the panel scratch (panel_slots_doubles() doubles, zeroed once per
-// factorisation): exchange slots for up to 256 SMs, the pivot log of one
-// panel (kPanelWidth words), then kInnerCounters words for the fused inner
-// update's per-column-tile counters.
-constexpr size_t kPanelExchangeDoubles = (size_t)2 * (256 + 1) * kPanelSlotW;
+// factorisation): exchange slots for up to kPanelMaxSms CTAs (two parities),
+// then kInnerCounters words for the fused inner update's per-column-tile
+// counters.
+constexpr size_t kPanelExchangeDoubles = (size_t)2 * (kPanelMaxSms + 1) * kPanelSlotW;
 constexpr int kInnerCounters = 64;
 
-// Exchange area of the panel kernel (slots for up to 256 SMs + pivot log).
-// It must be zeroed once before the first panel of a factorisation;
-// panel_index (distinct for every panel of one factorisation, < 2^25) tags the
-// words. A is the panel's top-left element (row = column = row0) of an
-// ncols-column matrix: besides factoring the panel, the launch applies the
-// panel's row interchanges to every other column of the matrix.
+// Exchange area of the panel kernels. It must be zeroed once before the
+// first panel of a factorisation; panel_index (distinct for every panel of
+// one factorisation, < 2^25) tags the words. A is the panel's top-left
+// element (row = column = row0, m rows below it including itself, w <= 32
+// columns). Besides factoring the panel, the launch applies the panel's row
+// interchanges to the nleft columns left of it and the nright columns right
+// of it (the rest of its outer block).
 size_t panel_slots_doubles();
 
 template <typename Ts>
 cudaError_t launch_panel(Ts* A, int lda, int m, int w, int row0, int* ipiv, int* info,
-                         double* slots, unsigned panel_index, int ncols, cudaStream_t s);
+                         double* slots, unsigned panel_index, int nleft, int nright,
+                         cudaStream_t s);
+
+// Row interchanges of one outer block (ipiv[0 .. kb): 1-based absolute rows,
+// the block starting at row k0, kb <= 256) applied, in order, to columns
+// [0, skip_lo) and [skip_hi, ncols) of the nrows x ncols matrix A. No waits.
+template <typename T>
+cudaError_t launch_laswp_block(T* A, int lda, int ncols, int nrows, int k0, int kb, const int* ipiv,
+                               int skip_lo, int skip_hi, cudaStream_t s);
 
 // B (w x N, ldb) <- L^{-1} B with L unit lower (w x w, ldl). Tc: arithmetic type.
 // out_kind: 0 none, GBLA_PREC_BF16/FP16/TF32 -> also write a K-major copy of
@@ -185,6 +202,9 @@ size_t mgs_slots_doubles();
 cudaError_t launch_mgs_step(int n, int j, double* V, int ldv, const double* w, double* H, int ldh,
                             double* cs, double* sn, double* g, void* st, double* slots,
                             unsigned* counter, int* info, cudaStream_t s);
+// out = a x + b y (FP64 vectors; out may alias x or y)
+cudaError_t launch_axpby(int n, double a, const double* x, double b, const double* y, double* out,
+                         cudaStream_t s);
 cudaError_t launch_gmres_update(int n, int k, const double* V, int ldv, const double* H, int ldh,
                                 const double* g, double* x, cudaStream_t s);
 

@@ -343,6 +343,23 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// out = a x + b y (FP64 vectors; out may alias x or y).
+__global__ void axpby_kernel(int n, double a, const double* x, double b, const double* y,
+                             double* out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    out[i] = fma(a, x[i], b * y[i]);
+}
+
+cudaError_t launch_axpby(int n, double a, const double* x, double b, const double* y, double* out,
+                         cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  int bx = (n + 255) / 256;
+  if (bx > 1024) bx = 1024;
+  axpby_kernel<<<bx, 256, 0, s>>>(n, a, x, b, y, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gmres_update(int n, int k, const double* V, int ldv, const double* H, int ldh,
                                 const double* g, double* x, cudaStream_t s) {
   if (n <= 0 || k <= 0) return cudaSuccess;

@@ -20,38 +20,38 @@
 
 namespace gbla {
 
-// Room for the panel kernel's exchange area on a device with up to
-// kStaticMaxSms multiprocessors: 2 * (SMs + 1) slots of kPanelSlotW doubles,
-// a pivot log of one word per panel column and the inner update's counters.
+// Room for the panel kernels' exchange area (two parities of slots for up to
+// kPanelMaxSms CTAs; the panel launcher never uses more CTAs than that, on
+// any device) and the inner update's counters.
 constexpr int kStaticMaxSms = 256;
+static_assert(kStaticMaxSms == kPanelMaxSms, "the fixed array follows the panel kernels' bound");
 constexpr size_t kStaticSlotsDoubles =
-    (size_t)2 * (kStaticMaxSms + 1) * kPanelSlotW + kPanelWidth + kInnerCounters / 2;
-constexpr size_t kStaticTotalDoubles = kStaticSlotsDoubles;
-constexpr size_t kStaticSlotsBytes = kStaticTotalDoubles * sizeof(double);
+    (size_t)2 * (kStaticMaxSms + 1) * kPanelSlotW + kInnerCounters / 2;
+constexpr size_t kStaticSlotsBytes = kStaticSlotsDoubles * sizeof(double);
 static_assert(kStaticSlotsBytes < 300 * 1024, "the fixed scratch is meant to stay below 300 KiB");
 
-static __device__ __align__(256) double g_static_slots[kStaticTotalDoubles];
+static __device__ __align__(256) double g_static_slots[kStaticSlotsDoubles];
 
-static double* static_slots_address(int device, cudaError_t* err) {
+static cudaError_t static_slots_address(int device, double** out) {
   static std::mutex mu;
   static double* addr[64] = {nullptr};
   std::lock_guard<std::mutex> lock(mu);
-  if (device < 0 || device >= 64) {
-    *err = cudaErrorInvalidDevice;
-    return nullptr;
-  }
+  if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
   if (!addr[device]) {
     void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_static_slots);
-    if (e != cudaSuccess) {
-      *err = e;
-      return nullptr;
-    }
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_slots);
+    if (e != cudaSuccess) return e;
     addr[device] = static_cast<double*>(p);
   }
-  *err = cudaSuccess;
-  return addr[device];
+  *out = addr[device];
+  return cudaSuccess;
 }
+
+#define NOALLOC_TRY(expr)                                                        \
+  do {                                                                           \
+    const int _st = api_cuda_status((expr), #expr, "noalloc.cu", __LINE__);      \
+    if (_st != GBLA_OK) return _st;                                              \
+  } while (0)
 
 }  // namespace gbla
 
@@ -59,6 +59,7 @@ using namespace gbla;
 
 extern "C" int gbla_lu_factor_static(int n, double* A, int lda, int* ipiv, int* d_info, int nb,
                                      gbla_stream_t stream) {
+  api_clear_error();
   if (n < 0) return -1;
   if (n > 0 && !A) return -2;
   if (lda < (n > 1 ? n : 1)) return -3;
@@ -67,28 +68,25 @@ extern "C" int gbla_lu_factor_static(int n, double* A, int lda, int* ipiv, int* 
   if (nb == 0) nb = 256;
   if (nb % 32 != 0 || nb < 32 || nb > 256) return -6;
   int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess) return GBLA_ERR_CUDA;
+  NOALLOC_TRY(cudaGetDevice(&dev));
   const DeviceProps& dp = device_props();
   if (dp.device < 0) return GBLA_ERR_CUDA;
   if (!dp.coop) return GBLA_ERR_DEVICE;
-  // the fixed array must hold every slot the panel kernel can use on this device
-  if (panel_slots_doubles() > kStaticSlotsDoubles)
-    return GBLA_ERR_WORKSPACE;
-  cudaError_t e;
-  double* slots = static_slots_address(dev, &e);
-  if (!slots) return GBLA_ERR_CUDA;
+  // the fixed array must hold every slot the panel kernels can use
+  if (panel_slots_doubles() > kStaticSlotsDoubles) return GBLA_ERR_WORKSPACE;
+  double* slots = nullptr;
+  NOALLOC_TRY(static_slots_address(dev, &slots));
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if (cudaMemsetAsync(d_info, 0, sizeof(int), s) != cudaSuccess) return GBLA_ERR_CUDA;
+  NOALLOC_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), s));
   if (n == 0) return GBLA_OK;
   // the array keeps the previous call's contents: stale slot tags must not
   // match this factorisation's, so the slots start from zero every call
-  if (cudaMemsetAsync(slots, 0, sizeof(double) * panel_slots_doubles(), s) != cudaSuccess)
-    return GBLA_ERR_CUDA;
+  NOALLOC_TRY(cudaMemsetAsync(slots, 0, sizeof(double) * panel_slots_doubles(), s));
   LuWork w;
   w.slots = slots;
   w.Ak = w.Bk = nullptr;
   w.eA = w.eB = nullptr;
   w.ldk = 0;
-  return blocked_lu<double>(n, A, lda, ipiv, d_info, nb, 0, w, s) == cudaSuccess ? GBLA_OK
-                                                                                  : GBLA_ERR_CUDA;
+  return api_cuda_status(blocked_lu<double>(n, A, lda, ipiv, d_info, nb, 0, w, s),
+                         "blocked_lu<double>", "noalloc.cu", __LINE__);
 }

@@ -1,9 +1,10 @@
 // Panel factorisation with partial pivoting (paper section 2, the GEPP step of
-// the blocked LU). Full-width panels of up to 16384 (FP32) or 4096 (FP64)
-// rows run in one thread-block cluster (the cluster variant further down);
-// the kernels described here take the others: an m x w panel (w <= 32) is
-// spread over C cooperative CTAs,
-// each holding a contiguous slab of R rows in shared memory in the storage
+// the blocked LU) and the row interchanges that go with it.
+//
+// Full-width panels of up to 16384 (FP32) or 4096 (FP64) rows run in one
+// thread-block cluster (the cluster variant further down); the kernels
+// described here take the others: an m x w panel (w <= 32) is spread over C
+// cooperative CTAs, each holding a contiguous slab of R rows in the storage
 // precision Ts, which is also the arithmetic precision (FP64 for the FP64
 // factorisation; FP32 for the low-precision one, every operation rounded to
 // FP32 as the working matrix is).
@@ -26,6 +27,13 @@
 // Slots are double-buffered by column parity: a CTA publishes column j + 2
 // only after it has seen every header of column j + 1, which each CTA writes
 // only after it has finished reading column j.
+//
+// Every panel launch also applies its interchanges to the other columns of
+// the current outer block (nleft columns to the left of the panel, nright to
+// its right) once its pivots are known; the columns outside the outer block
+// get all the interchanges of the block at once from laswp_block_kernel,
+// launched after the block's last panel. No CTA of any of these kernels waits
+// for a CTA that the hardware does not schedule with it.
 #include <climits>
 
 #include "common.cuh"
@@ -36,14 +44,9 @@ namespace gbla {
 constexpr int kPanelThreads = 256;
 constexpr int kSlotRow = 4;  // words before the row words in a slot (3 header words + pad)
 
-size_t panel_slots_doubles() { return kPanelExchangeDoubles + kPanelWidth + kInnerCounters / 2; }
+size_t panel_slots_doubles() { return kPanelExchangeDoubles + kInnerCounters / 2; }
 
 typedef unsigned long long u64;
-
-// Word offset of the pivot log in the exchange area (after 2 * (kMaxSms + 1)
-// slots); the host sizes the area with the same bound.
-constexpr int kPanelMaxSms = 256;
-GBLA_DEVINL size_t panel_pivlog_offset() { return (size_t)2 * (kPanelMaxSms + 1) * kPanelSlotW; }
 
 GBLA_DEVINL void st_relaxed_u64(u64* p, u64 v) {
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
@@ -202,50 +205,248 @@ GBLA_DEVINL void warp_merge_redux(PivKey<double>& p) {
   p.r = (int)~nr;
 }
 
-// Interchange role of the panel launch: the last S CTAs apply each column's
-// row interchange (rows j0 + j and j0 + p) to every column of the matrix
-// outside the panel, as soon as CTA 0 has logged the pivot of column j. They
-// only read the exchange (never publish), so they cannot slow the panel down;
-// each thread always owns the same columns, so program order keeps the
-// interchanges of one column in sequence.
-template <typename Ts>
-GBLA_DEVINL void swapper_role(Ts* __restrict__ Aall, int lda, int ncols, int j0, int w, int jend,
-                              int sidx, int S, const u64* __restrict__ pivlog, unsigned tag_base,
-                              int* __restrict__ info, uint64_t wait_ns) {
-  __shared__ int s_sp, s_sabort;
-  const int other = ncols - w;
-  const int per = (other + S - 1) / S;
-  const int cbeg = sidx * per, cend = min(other, cbeg + per);
-  for (int j = 0; j < jend; ++j) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const u64 tag = (u64)(tag_base | (unsigned)(j + 1)) << 32;
-      uint32_t pl[1] = {0};
-      s_sabort = ll_read<1>(pivlog + j, tag, wait_ns, pl) ? 0 : 1;
-      s_sp = (int)pl[0];
-    }
-    __syncthreads();
-    if (s_sabort) {
-      if (threadIdx.x == 0) gbla_flag_timeout(info);
-      return;
-    }
-    const int p = s_sp;
-    if (p == j) continue;
-    for (int q = cbeg + (int)threadIdx.x; q < cend; q += blockDim.x) {
-      const int col = q < j0 ? q : q + w;
-      Ts* a = Aall + (size_t)col * lda;
-      const Ts x = a[j0 + j];
-      a[j0 + j] = a[j0 + p];
-      a[j0 + p] = x;
+// ---------------------------------------------------------------------------
+// Row interchanges of one panel applied to a column outside it, one warp per
+// column (LAPACK laswp semantics: for l = 0 .. nw-1 in order, rows l and
+// piv_l of the column are exchanged; rows relative to the panel's first row,
+// piv_l >= l). Lane l holds piv_l. The plan is made once per warp: which of
+// the touched rows -- the nw top rows and every distinct partner row below
+// them -- ends up holding which row's old value. Applying it to a column is
+// then one load and one store per touched row, the top rows coalesced.
+//
+// Slots: top slot t (t < nw) is row t; outside slot 32 + l is row piv_l for
+// the first lane l naming a row piv_l >= nw. The plan simulates the nw
+// exchanges on slot identities (ct, co: the slot whose old value ends up in
+// this lane's top / outside slot).
+struct LaswpPlan {
+  int piv, nw, ct, co;
+  bool out;  // this lane owns an outside slot
+  GBLA_DEVINL void make(int piv_in, int nw_in, int lane) {
+    nw = nw_in;
+    piv = lane < nw ? piv_in : lane;
+    const bool outside = lane < nw && piv >= nw;
+    const unsigned same = __match_any_sync(0xffffffffu, outside ? piv : -1 - lane);
+    const int f = __ffs(same) - 1;  // first lane naming the same outside row
+    out = outside && f == lane;
+    ct = lane;
+    co = 32 + lane;
+    for (int j = 0; j < nw; ++j) {
+      const int pj = __shfl_sync(0xffffffffu, piv, j);
+      const int fj = __shfl_sync(0xffffffffu, f, j);
+      const bool top = pj < nw;
+      const int a = __shfl_sync(0xffffffffu, ct, j);
+      const int bt = __shfl_sync(0xffffffffu, ct, top ? pj : 0);
+      const int bo = __shfl_sync(0xffffffffu, co, top ? 0 : fj);
+      const int b = top ? bt : bo;
+      if (top) {
+        if (lane == pj) ct = a;
+      } else if (lane == fj) {
+        co = a;
+      }
+      if (lane == j) ct = b;
     }
   }
+  // col: the column's element in the panel's first row
+  template <typename T>
+  GBLA_DEVINL void apply(T* col, int lane) const {
+    const T vt = lane < nw ? col[lane] : (T)0;
+    const T vo = out ? col[piv] : (T)0;
+    store(col, lane, vt, vo);
+  }
+  // U columns at once: every load is issued before the first store, so the
+  // loads of the U columns are in flight together
+  template <typename T, int U>
+  GBLA_DEVINL void apply_n(T* const (&cols)[U], int lane) const {
+    T vt[U], vo[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      vt[u] = (cols[u] && lane < nw) ? cols[u][lane] : (T)0;
+      vo[u] = (cols[u] && out) ? cols[u][piv] : (T)0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (cols[u]) store(cols[u], lane, vt[u], vo[u]);
+  }
+  template <typename T>
+  GBLA_DEVINL void store(T* col, int lane, T vt, T vo) const {
+    const T x1 = __shfl_sync(0xffffffffu, vt, ct & 31);
+    const T x2 = __shfl_sync(0xffffffffu, vo, ct & 31);
+    const T y1 = __shfl_sync(0xffffffffu, vt, co & 31);
+    const T y2 = __shfl_sync(0xffffffffu, vo, co & 31);
+    if (lane < nw) col[lane] = ct < 32 ? x1 : x2;
+    if (out) col[piv] = co < 32 ? y1 : y2;
+  }
+};
+
+// The panel's interchanges on the other columns of its outer block: columns
+// -nleft .. -1 and w .. w + nright - 1 relative to the panel (A = its
+// top-left element), warp g of G.
+template <typename Ts>
+GBLA_DEVINL void panel_tail_swaps(Ts* A, int lda, int w, int nleft, int nright, const LaswpPlan& plan,
+                                  int g, int G, int lane) {
+  const int nt = nleft + nright;
+  for (int q0 = 2 * g; q0 < nt; q0 += 2 * G) {
+    Ts* cols[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int q = q0 + u;
+      const long long col = q < nleft ? (long long)q - nleft : (long long)w + (q - nleft);
+      cols[u] = q < nt ? A + col * lda : nullptr;
+    }
+    plan.apply_n<Ts, 2>(cols, lane);
+  }
 }
+
+// Interchanges of one outer block (ipiv[0 .. kb), 1-based absolute rows, the
+// block starting at row k0; kb <= 256) applied to columns [0, skip_lo) and
+// [skip_hi, ncols) of the nrows x ncols matrix (LAPACK laswp semantics, in
+// order). Every CTA first works out, once, where each touched row's final
+// value comes from: the slots are the kb rows of the block (slot t = row
+// k0 + t) and, for each partner row below the block, the slot kb + f of the
+// first interchange f that names it; one thread runs the kb exchanges on slot
+// identities in shared memory. Then, 32 columns at a time, the CTA loads the
+// touched rows of its columns into shared memory (the block's rows
+// coalesced, the partner rows one element per column) and writes each
+// touched row back from the slot that holds its final value. Columns are
+// never shared between CTAs; no waits. Pivots outside [row t, nrows) are
+// ignored.
+constexpr int kLbCols = 32;
+constexpr int kLbBatch = 16;  // loads a thread keeps in flight
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+    laswp_block_kernel(T* __restrict__ A, int lda, int ncols, int nrows, int k0, int kb,
+                       const int* __restrict__ ipiv, int skip_lo, int skip_hi) {
+  extern __shared__ double lb_smem[];
+  T* V = reinterpret_cast<T*>(lb_smem);                           // [2 kb][kLbCols + 1]
+  int* s_p = reinterpret_cast<int*>(V + (size_t)2 * kb * (kLbCols + 1));  // kb partner rows (relative)
+  int* s_f = s_p + kb;          // kb: first interchange naming the same outside row, or -1
+  int* s_row = s_f + kb;        // 2 kb: row of each slot (relative), -1 if unused
+  int* s_src = s_row + 2 * kb;  // 2 kb: slot whose old value ends up in this slot
+  int* s_list = s_src + 2 * kb; // 2 kb: the used slots, the block's rows first, in order
+  __shared__ int s_nv;
+  const int tid = threadIdx.x;
+  const int S = 2 * kb;
+  if (tid == 0) s_nv = kb;
+  for (int j = tid; j < kb; j += blockDim.x) {
+    int p = ipiv[j] - 1 - k0;
+    if (p < j || p >= nrows - k0) p = j;
+    s_p[j] = p;
+  }
+  __syncthreads();
+  for (int j = tid; j < kb; j += blockDim.x) {
+    const int p = s_p[j];
+    int f = -1;
+    if (p >= kb) {
+      f = j;
+      for (int k = 0; k < j; ++k)
+        if (s_p[k] == p) {
+          f = k;
+          break;
+        }
+    }
+    s_f[j] = f;
+    s_row[j] = j;
+    s_row[kb + j] = (f == j) ? p : -1;
+    s_list[j] = j;
+    if (f == j) s_list[atomicAdd(&s_nv, 1)] = kb + j;
+  }
+  for (int q = tid; q < S; q += blockDim.x) s_src[q] = q;
+  __syncthreads();
+  if (tid == 0) {
+    for (int j = 0; j < kb; ++j) {
+      const int p = s_p[j];
+      const int b = p < kb ? p : kb + s_f[j];
+      const int t = s_src[j];
+      s_src[j] = s_src[b];
+      s_src[b] = t;
+    }
+  }
+  __syncthreads();
+  const int nv = s_nv;
+  const int skip = skip_hi - skip_lo;
+  const int nfar = ncols - skip;
+  const int ntiles = (nfar + kLbCols - 1) / kLbCols;
+  const int total = nv * kLbCols;
+  T* base = A + k0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int q0 = tile * kLbCols;
+    // gather: kLbBatch independent loads per thread in flight, then the stores
+    for (int i0 = 0; i0 < total; i0 += 256 * kLbBatch) {
+      T v[kLbBatch];
+#pragma unroll
+      for (int u = 0; u < kLbBatch; ++u) {
+        const int idx = i0 + tid + 256 * u;
+        v[u] = (T)0;
+        if (idx < total) {
+          const int c = idx / nv, q = q0 + c;
+          if (q < nfar) {
+            const int col = q < skip_lo ? q : q + skip;
+            v[u] = base[(size_t)col * lda + s_row[s_list[idx - c * nv]]];
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kLbBatch; ++u) {
+        const int idx = i0 + tid + 256 * u;
+        if (idx < total) {
+          const int c = idx / nv;
+          V[(size_t)s_list[idx - c * nv] * (kLbCols + 1) + c] = v[u];
+        }
+      }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < total; idx += blockDim.x) {
+      const int c = idx / nv, q = q0 + c;
+      if (q < nfar) {
+        const int sl = s_list[idx - c * nv];
+        const int col = q < skip_lo ? q : q + skip;
+        base[(size_t)col * lda + s_row[sl]] = V[(size_t)s_src[sl] * (kLbCols + 1) + c];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+cudaError_t launch_laswp_block(T* A, int lda, int ncols, int nrows, int k0, int kb, const int* ipiv,
+                               int skip_lo, int skip_hi, cudaStream_t s) {
+  const int nfar = ncols - (skip_hi - skip_lo);
+  if (nfar <= 0 || kb <= 0) return cudaSuccess;
+  if (kb > 256) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)2 * kb * (kLbCols + 1) * sizeof(T) + (size_t)8 * kb * sizeof(int);
+  cudaError_t e = ensure_dyn_smem(laswp_block_kernel<T>, smem);
+  if (e != cudaSuccess) return e;
+  const DeviceProps& dp = device_props();
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, laswp_block_kernel<T>, 256, smem) !=
+          cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  const int ntiles = (nfar + kLbCols - 1) / kLbCols;
+  int grid = per_sm * (dp.num_sms > 0 ? dp.num_sms : 1);
+  if (grid > ntiles) grid = ntiles;
+  laswp_block_kernel<T><<<grid, 256, smem, s>>>(A, lda, ncols, nrows, k0, kb, ipiv, skip_lo, skip_hi);
+  count_launch();
+  return cudaGetLastError();
+}
+template cudaError_t launch_laswp_block<double>(double*, int, int, int, int, int, const int*, int,
+                                                int, cudaStream_t);
+template cudaError_t launch_laswp_block<float>(float*, int, int, int, int, int, const int*, int, int,
+                                               cudaStream_t);
+
+// The exchange area holds two parities of slots for up to kPanelMaxSms CTAs;
+// the launcher never uses more CTAs than that.
+static_assert(kPanelExchangeDoubles == (size_t)2 * (kPanelMaxSms + 1) * kPanelSlotW,
+              "exchange area sized for kPanelMaxSms CTAs");
 
 template <typename Ts>
 __global__ void __launch_bounds__(kPanelThreads)
     panel_kernel(Ts* __restrict__ A, int lda, int m, int w, int row0, int R,
                  int* __restrict__ ipiv, int* __restrict__ info, double* __restrict__ slots_d,
-                 unsigned tag_base, uint64_t wait_ns, int ncols, int S) {
+                 unsigned tag_base, uint64_t wait_ns, int nleft, int nright) {
   typedef PivKey<Ts> Key;
   constexpr int KW = Key::kWords;
   extern __shared__ double smem[];
@@ -261,14 +462,7 @@ __global__ void __launch_bounds__(kPanelThreads)
   __shared__ int s_abort;
 
   u64* slots = reinterpret_cast<u64*>(slots_d);
-  const int C = gridDim.x - S;  // panel CTAs; the last S CTAs apply the interchanges
-  if ((int)blockIdx.x >= C) {
-    swapper_role<Ts>(A - (size_t)row0 - (size_t)row0 * lda, lda, ncols, row0, w, min(w, m),
-                     (int)blockIdx.x - C, S,
-                     reinterpret_cast<const u64*>(slots_d) + panel_pivlog_offset(), tag_base, info,
-                     wait_ns);
-    return;
-  }
+  const int C = gridDim.x;
   const int c = blockIdx.x;
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
@@ -288,6 +482,7 @@ __global__ void __launch_bounds__(kPanelThreads)
   __syncthreads();
 
   const int jend = min(w, m);
+  int my_piv = lane;  // lane l: the partner row of column l
   for (int j = 0; j < jend; ++j) {
     const int par = j & 1;
     const u64 tag = (u64)(tag_base | (unsigned)(j + 1)) << 32;
@@ -352,6 +547,7 @@ __global__ void __launch_bounds__(kPanelThreads)
     __syncthreads();
     const Key gk = s_key;
     const int p = gk.row();
+    if (lane == j) my_piv = p;
     const int cw = p / R;  // the CTA that owns row p published it
     const bool own_j = (j >= rbeg && j < rbeg + rcnt);
     const bool own_p = (p >= rbeg && p < rbeg + rcnt);
@@ -377,8 +573,6 @@ __global__ void __launch_bounds__(kPanelThreads)
     }
     if (c == 0 && tid == 0) {
       ipiv[j] = row0 + p + 1;
-      if (S > 0)
-        st_relaxed_u64(slots + panel_pivlog_offset() + j, tag | (u64)(unsigned)p);
       if (gk.zero_pivot()) atomicCAS(info, 0, row0 + j + 1);
     }
     __syncthreads();
@@ -415,6 +609,11 @@ __global__ void __launch_bounds__(kPanelThreads)
   for (int k = 0; k < w; ++k)
     for (int r = tid; r < rcnt; r += blockDim.x)
       A[(size_t)k * lda + rbeg + r] = slab[k * R + r];
+  if (nleft + nright > 0) {
+    LaswpPlan plan;
+    plan.make(my_piv, jend, lane);
+    panel_tail_swaps<Ts>(A, lda, w, nleft, nright, plan, c * nwarps + warp, C * nwarps, lane);
+  }
 }
 
 // Register-resident variant: thread t of a CTA holds rows t, t + 256, ...
@@ -426,7 +625,7 @@ template <typename Ts, int RPT>
 __global__ void __launch_bounds__(kPanelThreads, 1)
     panel_reg_kernel(Ts* __restrict__ A, int lda, int m, int w, int row0, int R,
                      int* __restrict__ ipiv, int* __restrict__ info, double* __restrict__ slots_d,
-                     unsigned tag_base, uint64_t wait_ns, int ncols, int S) {
+                     unsigned tag_base, uint64_t wait_ns, int nleft, int nright) {
   typedef PivKey<Ts> Key;
   constexpr int KW = Key::kWords;
   constexpr int W = kPanelWidth;
@@ -440,14 +639,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
   __shared__ int s_abort;
 
   u64* slots = reinterpret_cast<u64*>(slots_d);
-  const int C = gridDim.x - S;  // panel CTAs; the last S CTAs apply the interchanges
-  if ((int)blockIdx.x >= C) {
-    swapper_role<Ts>(A - (size_t)row0 - (size_t)row0 * lda, lda, ncols, row0, w, min(w, m),
-                     (int)blockIdx.x - C, S,
-                     reinterpret_cast<const u64*>(slots_d) + panel_pivlog_offset(), tag_base, info,
-                     wait_ns);
-    return;
-  }
+  const int C = gridDim.x;
   const int c = blockIdx.x;
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
@@ -470,6 +662,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
   __syncthreads();
 
   const int jend = min(w, m);
+  int my_piv = lane;  // lane l: the partner row of column l
 #pragma unroll
   for (int j = 0; j < W; ++j) {
     if (j < jend) {
@@ -550,6 +743,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
       __syncthreads();
       const Key gk = s_key;
       const int p = gk.row();
+      if (lane == j) my_piv = p;
       const int cw = p / R;
       const bool own_p = (p >= rbeg && p < rbeg + rcnt);
       // 4. pivot row (and old row j for the owner of row p)
@@ -574,8 +768,6 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
       }
       if (c == 0 && tid == 0) {
         ipiv[j] = row0 + p + 1;
-      if (S > 0)
-        st_relaxed_u64(slots + panel_pivlog_offset() + j, tag | (u64)(unsigned)p);
         if (gk.zero_pivot()) atomicCAS(info, 0, row0 + j + 1);
       }
       if (tid >= kPanelWidth * 2 && tid < kPanelWidth * 2 + kPanelWidth)  // pad columns >= w
@@ -621,26 +813,43 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
     for (int k = 0; k < W; ++k)
       if (r < rcnt && k < w) A[(size_t)k * lda + rbeg + r] = a[i][k];
   }
+  if (nleft + nright > 0) {
+    LaswpPlan plan;
+    plan.make(my_piv, jend, lane);
+    panel_tail_swaps<Ts>(A, lda, w, nleft, nright, plan, c * nwarps + warp, C * nwarps, lane);
+  }
 }
 
 // ---------------------------------------------------------------------------
 // Cluster variant. The panel rows are spread over the CL CTAs (CL <= 16) of
-// one thread-block cluster, RPT (1 or 2) rows per thread, all kPanelWidth
-// columns in registers; the three argmax levels (thread -> warp -> CTA ->
-// cluster) use the warp's integer max reduction. The per-column exchange stays inside the cluster: every CTA
-// pushes its candidate (pivot key + row) into the shared memory of every CTA
-// of the cluster with st.async, completing bytes on the receiver's mbarrier,
-// and CTA 0 pushes old row j the same way; each CTA then waits on its own
-// mbarrier alone and reduces the CL candidates locally. Nothing goes through
-// global memory except the pivot log read by the interchange CTAs, which form
-// further clusters of the same cooperative launch.
+// one thread-block cluster -- the whole grid, scheduled together by the
+// hardware -- RPT (1 or 2) rows per thread, all kPanelWidth columns in
+// registers; the three argmax levels (thread -> warp -> CTA -> cluster) use
+// the warp's integer max reduction. The per-column exchange stays inside the
+// cluster: every CTA pushes its candidate (pivot key + row) into the shared
+// memory of every CTA of the cluster with a bulk copy, completing bytes on
+// the receiver's mbarrier, and CTA 0 pushes old row j the same way; each CTA
+// then waits on its own mbarrier alone and reduces the CL candidates locally.
+// Nothing goes through global memory.
 //
 // Buffers are double-buffered by column parity. A CTA pushes column j + 2
 // only after it has received every CTA's column j + 1 message, and each CTA
 // sends that message only after it has finished reading its column j
 // buffers; a CTA re-arms the mbarrier of column j + 2 before it sends its own
 // column j + 1 message, so the transaction count is always armed before any
-// byte of that column can arrive.
+// byte of that column can arrive. Hence, whenever a CTA stops, copies can be
+// on their way into it for at most the two columns its two mbarriers are
+// armed for.
+//
+// Leaving. Whether the panel finished or a wait gave up, every CTA tells
+// every other how many columns it pushed (shared-memory stores across the
+// cluster, made visible by a cluster barrier). From those counts a CTA knows
+// exactly how many bytes will still arrive for each armed column; it
+// completes the bytes that never will on its own mbarrier, waits (bounded)
+// for the phase to finish -- i.e. for every copy in flight into it to land --
+// and only then meets the others at a second cluster barrier. After that no
+// copy reads or writes the shared memory of any CTA of the cluster, so all
+// may exit.
 constexpr int kClMax = 16;
 
 template <typename Ts>
@@ -667,6 +876,9 @@ GBLA_DEVINL void cl_bulk_push(uint32_t rdst, uint32_t src, uint32_t bytes, uint3
       "r"(src), "r"(bytes), "r"(rbar)
       : "memory");
 }
+GBLA_DEVINL void cl_store_remote_u32(uint32_t raddr, uint32_t v) {
+  asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(raddr), "r"(v) : "memory");
+}
 GBLA_DEVINL void cl_fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -676,6 +888,10 @@ GBLA_DEVINL void cl_mbar_init(uint32_t bar, uint32_t count) {
 GBLA_DEVINL void cl_mbar_arm(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                : "memory");
+}
+// Count `bytes` as arrived on this CTA's mbarrier (bytes that no copy will bring).
+GBLA_DEVINL void cl_mbar_complete_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.complete_tx.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 GBLA_DEVINL bool cl_mbar_try(uint32_t bar, uint32_t parity) {
   uint32_t ok;
@@ -687,7 +903,21 @@ GBLA_DEVINL bool cl_mbar_try(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+GBLA_DEVINL bool cl_mbar_test(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase of the given parity. A limit of 0 does not wait
+// at all (one non-blocking test), so that "give up at once" is what it says:
+// try_wait may itself suspend the thread for a while before it answers.
 GBLA_DEVINL bool cl_mbar_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+  if (limit_ns == 0) return cl_mbar_test(bar, parity);
   if (cl_mbar_try(bar, parity)) return true;
   const uint64_t t0 = gbla_now_ns();
   while (!cl_mbar_try(bar, parity))
@@ -711,10 +941,8 @@ GBLA_DEVINL void cl_sync() {
 
 template <typename Ts, int NT, int RPT>
 __global__ void __launch_bounds__(NT, 1)
-    panel_cluster_kernel(Ts* __restrict__ A, int lda, int m, int row0,
-                         int* __restrict__ ipiv, int* __restrict__ info,
-                         double* __restrict__ slots_d, unsigned tag_base, uint64_t wait_ns,
-                         int ncols, int CL) {
+    panel_cluster_kernel(Ts* __restrict__ A, int lda, int m, int row0, int* __restrict__ ipiv,
+                         int* __restrict__ info, uint64_t wait_ns, int nleft, int nright, int CL) {
   typedef PivKey<Ts> Key;
   constexpr int W = kPanelWidth;
   constexpr int NW = NT / 32;
@@ -723,26 +951,21 @@ __global__ void __launch_bounds__(NT, 1)
   __shared__ alignas(16) Ts s_rowj[2][W];              // row j staged by its owner
   __shared__ alignas(16) Ts s_rowj_recv[2][W];         // row j pushed by CTA 0
   __shared__ alignas(8) u64 s_bar[2];
-  __shared__ int s_abort;
+  __shared__ unsigned s_pushed[kClMax];                // columns each CTA pushed (for leaving)
 
-  const u64* pivlog_r = reinterpret_cast<const u64*>(slots_d) + panel_pivlog_offset();
-  const int S = (int)gridDim.x - CL;
-  if ((int)blockIdx.x >= CL) {
-    swapper_role<Ts>(A - (size_t)row0 - (size_t)row0 * lda, lda, ncols, row0, W, W,
-                     (int)blockIdx.x - CL, S, pivlog_r, tag_base, info, wait_ns);
-    return;
-  }
-  u64* pivlog = reinterpret_cast<u64*>(slots_d) + panel_pivlog_offset();
-  // every shared-memory address below is mapped into CTAs 0 .. CL - 1 of this
-  // cluster: a launch whose clusters are not CL CTAs wide (never made by this
-  // library's launcher) does no exchange at all and reports a failed wait
-  if (cl_nctarank() != (uint32_t)CL || cl_ctarank() != blockIdx.x) {
-    if (threadIdx.x == 0) gbla_flag_timeout(info);
-    return;
-  }
-  const int c = blockIdx.x;  // rank in the panel cluster (cluster 0)
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
+  // pivots start as "no interchange" before anything can fail, so that an
+  // aborted launch leaves only in-range row indices behind
+  if (blockIdx.x == 0 && tid < W) ipiv[tid] = row0 + tid + 1;
+  // every shared-memory address below is mapped into CTAs 0 .. CL - 1 of this
+  // cluster: a launch whose cluster is not the CL-CTA grid (never made by this
+  // library's launcher) touches no other CTA and reports a failed wait
+  if (cl_nctarank() != (uint32_t)CL || cl_ctarank() != blockIdx.x || gridDim.x != (unsigned)CL) {
+    if (tid == 0) gbla_flag_timeout(info);
+    return;
+  }
+  const int c = blockIdx.x;  // rank in the cluster
   const int g0 = c * NT * RPT + tid;  // panel row of this thread's row i: g0 + i * NT
   const uint32_t kExpect = (uint32_t)(CL * sizeof(ClMsg<Ts>) + W * sizeof(Ts));
 
@@ -759,15 +982,15 @@ __global__ void __launch_bounds__(NT, 1)
     cl_mbar_init(bar[1], 1);
     cl_mbar_arm(bar[0], kExpect);
     cl_mbar_arm(bar[1], kExpect);
-    s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // pivots start as "no interchange", so that an aborted launch leaves only
-  // in-range row indices behind for the kernels that follow
-  if (c == 0 && tid < W) ipiv[tid] = row0 + tid + 1;
   cl_sync();  // every mbarrier initialised and armed before the first push
 
-  bool aborted = false;
+  int my_fail = 0;             // this thread's wait gave up
+  bool aborted = false;        // uniform over the CTA
+  int npushed = 0;             // columns this CTA pushed (uniform)
+  int armed[2] = {0, 1};       // thread 0: the column each mbarrier is armed for
+  int my_piv = lane;           // lane l: the partner row of column l
 #pragma unroll
   for (int j = 0; j < W; ++j) {
     const int par = j & 1;
@@ -797,7 +1020,11 @@ __global__ void __launch_bounds__(NT, 1)
     Key wk = bk;
     warp_merge_redux(wk);
     ClMsg<Ts>& mine = s_warp[par][warp];
-    if (bk.valid() && bk.same(wk)) {
+    // A thread whose wait of column j - 1 gave up stages nothing: only a
+    // completed column j - 1 proves that every copy of column j - 2 (which
+    // read this buffer) has landed. The CTA stops at the barrier below.
+    if (my_fail) {
+    } else if (bk.valid() && bk.same(wk)) {
       bk.to_pair(mine.k, mine.r);
 #pragma unroll
       for (int i = 0; i < RPT; ++i)
@@ -818,7 +1045,7 @@ __global__ void __launch_bounds__(NT, 1)
       Key().to_pair(mine.k, mine.r);
       cl_fence_proxy_async();
     }
-    if (c == 0 && tid == j) {
+    if (c == 0 && tid == j && !my_fail) {
       if constexpr (sizeof(Ts) == 4) {
 #pragma unroll
         for (int q = 0; q < W / 4; ++q)
@@ -831,8 +1058,8 @@ __global__ void __launch_bounds__(NT, 1)
       }
       cl_fence_proxy_async();
     }
-    __syncthreads();
-    if (s_abort) {
+    // one decision for the whole CTA: a wait of an earlier column gave up
+    if (__syncthreads_or(my_fail)) {
       aborted = true;
       break;
     }
@@ -854,12 +1081,15 @@ __global__ void __launch_bounds__(NT, 1)
         cl_bulk_push(cl_mapa(cl_smem_u32(s_rowj_recv[par]), lane), cl_smem_u32(s_rowj[par]),
                      (uint32_t)(W * sizeof(Ts)), cl_mapa(bar[par], lane));
     }
+    npushed = j + 1;
     // 3. wait for the CL candidates and row j; every warp reduces them
-    const bool ok = cl_mbar_wait(bar[par], (uint32_t)((j >> 1) & 1), wait_ns);
-    if (!ok) {
-      s_abort = 1;
+    if (!cl_mbar_wait(bar[par], (uint32_t)((j >> 1) & 1), wait_ns)) {
+      my_fail = 1;
     } else {
-      if (tid == 0 && j + 2 < W) cl_mbar_arm(bar[par], kExpect);
+      if (tid == 0 && j + 2 < W) {
+        cl_mbar_arm(bar[par], kExpect);
+        armed[par] = j + 2;
+      }
       Key q;
       Ts qv = (Ts)0;
       if (lane < CL) {
@@ -874,13 +1104,16 @@ __global__ void __launch_bounds__(NT, 1)
       const unsigned bal = __ballot_sync(0xffffffffu, lane < CL && q.same(g));
       const int cw = bal ? __ffs(bal) - 1 : 0;
       const int p = g.row();
+      // a winner outside rows j .. m-1 cannot come from a completed exchange;
+      // it is treated as a failed wait and never reaches ipiv
+      const bool pok = p >= j && p < m;
+      if (!pok) my_fail = 1;
+      if (lane == j) my_piv = pok ? p : j;
       const Ts* prow = s_recv[par][cw].v;
       const Ts pv = __shfl_sync(0xffffffffu, qv, cw);
       const Ts rp = __shfl_sync(0xffffffffu, qr, cw);
-      if (c == 0 && tid == 0) {
+      if (c == 0 && tid == 0 && pok) {
         ipiv[j] = row0 + p + 1;
-        if (S > 0)
-          st_relaxed_u64(pivlog + j, ((u64)(tag_base | (unsigned)(j + 1)) << 32) | (u64)(unsigned)p);
         if (g.zero_pivot()) atomicCAS(info, 0, row0 + j + 1);
       }
       // 4. interchange rows j and p, scale by the reciprocal pivot, rank-1
@@ -940,6 +1173,7 @@ __global__ void __launch_bounds__(NT, 1)
       }
     }
   }
+  if (!aborted) aborted = __syncthreads_or(my_fail) != 0;  // a wait of the last column
   if (!aborted) {
 #pragma unroll
     for (int i = 0; i < RPT; ++i) {
@@ -948,26 +1182,54 @@ __global__ void __launch_bounds__(NT, 1)
       for (int k = 0; k < W; ++k)
         if (gi < m) A[(size_t)k * lda + gi] = a[i][k];
     }
+    if (nleft + nright > 0) {
+      LaswpPlan plan;
+      plan.make(my_piv, W, lane);
+      panel_tail_swaps<Ts>(A, lda, W, nleft, nright, plan, c * NW + warp, CL * NW, lane);
+    }
   } else if (tid == 0) {
     gbla_flag_timeout(info);
   }
-  // no CTA leaves while a peer may still write into its shared memory
+  // Leaving (see above): publish the push count (top bit: this CTA stopped
+  // early) to every CTA. When no CTA stopped early, every copy of the launch
+  // has been waited for by its receiver, so the barrier that makes the counts
+  // visible is the last one. Otherwise each CTA drains the two armed columns
+  // of its mbarriers, then all meet at a final cluster barrier.
+  if (tid < CL)
+    cl_store_remote_u32(cl_mapa(cl_smem_u32(&s_pushed[c]), tid),
+                        (unsigned)npushed | (aborted ? 0x80000000u : 0u));
   cl_sync();
-  if (aborted) {
-    const uint64_t t0 = gbla_now_ns();
-    while (gbla_now_ns() - t0 < 20000) {
+  bool any_stopped = false;
+  for (int q = 0; q < CL; ++q) any_stopped = any_stopped || (s_pushed[q] & 0x80000000u) != 0;
+  if (!any_stopped) return;  // the same decision in every CTA of the cluster
+  if (tid == 0) {
+    // every copy counted here has been issued and lands within microseconds;
+    // the floor keeps a tiny caller wait limit from cutting the drain short
+    const uint64_t drain_ns = wait_ns > 200000000ull ? wait_ns : 200000000ull;
+    bool drained = true;
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const int col = armed[b];
+      uint32_t coming = 0;
+      for (int q = 0; q < CL; ++q)
+        if ((int)(s_pushed[q] & 0x7fffffffu) > col) coming += (uint32_t)sizeof(ClMsg<Ts>);
+      if ((int)(s_pushed[0] & 0x7fffffffu) > col) coming += (uint32_t)(W * sizeof(Ts));
+      if (coming < kExpect) cl_mbar_complete_tx(bar[b], kExpect - coming);
+      drained = cl_mbar_wait(bar[b], (uint32_t)((col >> 1) & 1), drain_ns) && drained;
     }
+    if (!drained) gbla_flag_timeout(info);
   }
+  __syncthreads();
+  cl_sync();
 }
 
 template <typename Ts, int NT, int RPT>
-static cudaError_t launch_panel_cluster_nt(Ts* A, int lda, int m, int row0, int* ipiv,
-                                           int* info, double* slots, unsigned tag_base,
-                                           uint64_t wait_ns, int ncols, int CL, int S,
+static cudaError_t launch_panel_cluster_nt(Ts* A, int lda, int m, int row0, int* ipiv, int* info,
+                                           uint64_t wait_ns, int nleft, int nright, int CL,
                                            cudaStream_t s) {
-  // once per device: allow clusters of 16 and look up how many clusters of
-  // each size can be resident, so that a launch that cannot be co-resident
-  // is never attempted
+  // once per device: allow clusters of 16 and look up whether a cluster of
+  // each size can be resident, so that a launch that cannot be placed is
+  // never attempted
   static int max_clusters[64][kClMax + 1];
   static bool init[64] = {false};
   const int dev = device_props().device;
@@ -982,16 +1244,16 @@ static cudaError_t launch_panel_cluster_nt(Ts* A, int lda, int m, int row0, int*
     for (int i = 0; i <= kClMax; ++i) max_clusters[dev][i] = -1;
     init[dev] = true;
   }
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
   if (max_clusters[dev][CL] < 0) {
     cudaLaunchConfig_t q = {};
     q.gridDim = dim3((unsigned)CL);
     q.blockDim = dim3(NT);
-    cudaLaunchAttribute qa[1];
-    qa[0].id = cudaLaunchAttributeClusterDimension;
-    qa[0].val.clusterDim.x = (unsigned)CL;
-    qa[0].val.clusterDim.y = 1;
-    qa[0].val.clusterDim.z = 1;
-    q.attrs = qa;
+    q.attrs = at;
     q.numAttrs = 1;
     int n = 0;
     if (cudaOccupancyMaxActiveClusters(&n, panel_cluster_kernel<Ts, NT, RPT>, &q) != cudaSuccess) {
@@ -1000,38 +1262,29 @@ static cudaError_t launch_panel_cluster_nt(Ts* A, int lda, int m, int row0, int*
     }
     max_clusters[dev][CL] = n;
   }
-  if (max_clusters[dev][CL] < 1 + S / CL) return cudaErrorNotSupported;
+  if (max_clusters[dev][CL] < 1) return cudaErrorNotSupported;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(CL + S));
+  cfg.gridDim = dim3((unsigned)CL);  // one cluster: the whole grid
   cfg.blockDim = dim3(NT);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
-  cudaLaunchAttribute at[2];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = (unsigned)CL;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  at[1].id = cudaLaunchAttributeCooperative;
-  at[1].val.cooperative = 1;
   cfg.attrs = at;
-  cfg.numAttrs = 2;
+  cfg.numAttrs = 1;
   count_launch();
   return cudaLaunchKernelEx(&cfg, panel_cluster_kernel<Ts, NT, RPT>, A, lda, m, row0, ipiv, info,
-                            slots, tag_base, wait_ns, ncols, CL);
+                            wait_ns, nleft, nright, CL);
 }
 
 // Cluster launch shape for a full-width panel of m >= 32 rows: NT threads
 // per CTA (128, 256 or 512) with RPT rows each (2 only for FP32 panels of
-// more than 8192 rows), CL = the power of two >= m / (NT * RPT), and enough
-// interchange CTAs (a multiple of CL, at most 64) for about one column per
-// thread. An FP64 row takes twice the registers, so FP64 stays at <= 256
-// threads.
+// more than 8192 rows) and CL = the power of two >= m / (NT * RPT) CTAs. An
+// FP64 row takes twice the registers, so FP64 stays at <= 256 threads.
 // Returns cudaErrorNotSupported, with nothing enqueued, for a narrower or
-// taller panel or when the device cannot hold the launch.
+// taller panel or when the device cannot hold the cluster.
 template <typename Ts>
 static cudaError_t launch_panel_cluster(Ts* A, int lda, int m, int w, int row0, int* ipiv,
-                                        int* info, double* slots, unsigned tag_base,
-                                        uint64_t wait_ns, int ncols, cudaStream_t s) {
+                                        int* info, uint64_t wait_ns, int nleft, int nright,
+                                        cudaStream_t s) {
   constexpr int kMaxNt = sizeof(Ts) == 4 ? 512 : 256;
   constexpr int kMaxRpt = sizeof(Ts) == 4 ? 2 : 1;
   if (w != kPanelWidth || m < kPanelWidth) return cudaErrorNotSupported;
@@ -1042,92 +1295,78 @@ static cudaError_t launch_panel_cluster(Ts* A, int lda, int m, int w, int row0, 
   const int need = (m + NT * RPT - 1) / (NT * RPT);
   int CL = 1;
   while (CL < need) CL *= 2;
-  const int other = ncols - w;
-  int S = 0;
-  if (other > 0) {
-    S = (other + NT - 1) / NT;
-    if (S > 64) S = 64;
-    S = ((S + CL - 1) / CL) * CL;
-  }
   if (RPT == 2) {
     if constexpr (sizeof(Ts) == 4)
-      return launch_panel_cluster_nt<Ts, 512, 2>(A, lda, m, row0, ipiv, info, slots, tag_base, wait_ns, ncols, CL, S, s);
+      return launch_panel_cluster_nt<Ts, 512, 2>(A, lda, m, row0, ipiv, info, wait_ns, nleft, nright, CL, s);
     return cudaErrorNotSupported;
   }
   switch (NT) {
     case 128:
-      return launch_panel_cluster_nt<Ts, 128, 1>(A, lda, m, row0, ipiv, info, slots, tag_base, wait_ns, ncols, CL, S, s);
+      return launch_panel_cluster_nt<Ts, 128, 1>(A, lda, m, row0, ipiv, info, wait_ns, nleft, nright, CL, s);
     case 256:
-      return launch_panel_cluster_nt<Ts, 256, 1>(A, lda, m, row0, ipiv, info, slots, tag_base, wait_ns, ncols, CL, S, s);
+      return launch_panel_cluster_nt<Ts, 256, 1>(A, lda, m, row0, ipiv, info, wait_ns, nleft, nright, CL, s);
     default:
       if constexpr (sizeof(Ts) == 4)
-        return launch_panel_cluster_nt<Ts, 512, 1>(A, lda, m, row0, ipiv, info, slots, tag_base, wait_ns, ncols, CL, S, s);
+        return launch_panel_cluster_nt<Ts, 512, 1>(A, lda, m, row0, ipiv, info, wait_ns, nleft, nright, CL, s);
       return cudaErrorNotSupported;
   }
 }
 
 template <typename Ts>
 cudaError_t launch_panel(Ts* A, int lda, int m, int w, int row0, int* ipiv, int* info,
-                         double* slots, unsigned panel_index, int ncols, cudaStream_t s) {
+                         double* slots, unsigned panel_index, int nleft, int nright,
+                         cudaStream_t s) {
   if (m <= 0 || w <= 0) return cudaSuccess;
-  if (w > kPanelWidth) return cudaErrorInvalidValue;
+  if (w > kPanelWidth || nleft < 0 || nright < 0) return cudaErrorInvalidValue;
   const DeviceProps& dp = device_props();
   if (dp.device < 0) return cudaErrorNoDevice;
+  const uint64_t wait_ns = wait_timeout_ns();
   {
-    const cudaError_t ec = launch_panel_cluster<Ts>(A, lda, m, w, row0, ipiv, info, slots,
-                                                    (panel_index + 1u) << 6, wait_timeout_ns(),
-                                                    ncols, s);
+    const cudaError_t ec =
+        launch_panel_cluster<Ts>(A, lda, m, w, row0, ipiv, info, wait_ns, nleft, nright, s);
     if (ec != cudaErrorNotSupported) return ec;
   }
   // Panels taller than one cluster holds: up to 64 CTAs exchanging through
-  // global memory. Up to 64 CTAs: the exchange round per column gets slower with the number
-  // of CTAs polling each other's headers, faster than the per-CTA share of
-  // the rank-1 update grows (measured at m = 16384: 3.96 us per column with
-  // 64 CTAs, 4.79 us with 152).
+  // global memory, all resident together (a cooperative launch). Up to 64
+  // CTAs: the exchange round per column gets slower with the number of CTAs
+  // polling each other's headers, faster than the per-CTA share of the
+  // rank-1 update grows (measured at m = 16384: 3.96 us per column with 64
+  // CTAs, 4.79 us with 152).
   const int kMinRows = 64, kMaxCtas = 64;
+  const int max_ctas = dp.num_sms < kPanelMaxSms ? dp.num_sms : kPanelMaxSms;
   int C = (m + kMinRows - 1) / kMinRows;
   if (C > kMaxCtas) C = kMaxCtas;
-  if (C > dp.num_sms) C = dp.num_sms;
+  if (C > max_ctas) C = max_ctas;
   if (C < 1) C = 1;
   int R = (m + C - 1) / C;
   if (R > 2 * kPanelThreads) {  // more CTAs before leaving the register-resident kernel
     C = (m + 2 * kPanelThreads - 1) / (2 * kPanelThreads);
-    if (C > dp.num_sms) C = dp.num_sms;
+    if (C > max_ctas) C = max_ctas;
     R = (m + C - 1) / C;
   }
   C = (m + R - 1) / R;
-  // interchange CTAs: enough that each owns ~512 of the other columns, while
-  // the whole grid stays co-resident (one CTA per SM)
-  int S = 0;
-  if (ncols > w) {
-    S = (ncols - w + 511) / 512;
-    if (S > 32) S = 32;
-    if (S > dp.num_sms - C) S = dp.num_sms - C;
-    if (S < 1) S = 0;  // no room: caller must apply the interchanges itself
-  }
-  if (S == 0 && ncols > w) return cudaErrorInvalidConfiguration;
-  uint64_t wait_ns = wait_timeout_ns();
   unsigned tag_base = (panel_index + 1u) << 6;
-  void* args[] = {&A, &lda, &m, &w, &row0, &R, &ipiv, &info, &slots, &tag_base, &wait_ns, &ncols, &S};
+  uint64_t wns = wait_ns;
+  void* args[] = {&A, &lda, &m, &w, &row0, &R, &ipiv, &info, &slots, &tag_base, &wns, &nleft, &nright};
   count_launch();
   if (R <= kPanelThreads)
-    return cudaLaunchCooperativeKernel((const void*)panel_reg_kernel<Ts, 1>, dim3(C + S),
+    return cudaLaunchCooperativeKernel((const void*)panel_reg_kernel<Ts, 1>, dim3(C),
                                        dim3(kPanelThreads), args, 0, s);
   if (R <= 2 * kPanelThreads)
-    return cudaLaunchCooperativeKernel((const void*)panel_reg_kernel<Ts, 2>, dim3(C + S),
+    return cudaLaunchCooperativeKernel((const void*)panel_reg_kernel<Ts, 2>, dim3(C),
                                        dim3(kPanelThreads), args, 0, s);
   // very tall panels: shared-memory slab
   size_t smem = ((size_t)w * R + 2 * kPanelWidth) * sizeof(Ts) + 16;
   if (smem > dp.smem_optin) return cudaErrorInvalidValue;
   cudaError_t ea = ensure_dyn_smem(panel_kernel<Ts>, smem);
   if (ea != cudaSuccess) return ea;
-  return cudaLaunchCooperativeKernel((const void*)panel_kernel<Ts>, dim3(C + S), dim3(kPanelThreads),
+  return cudaLaunchCooperativeKernel((const void*)panel_kernel<Ts>, dim3(C), dim3(kPanelThreads),
                                      args, smem, s);
 }
 
 template cudaError_t launch_panel<double>(double*, int, int, int, int, int*, int*, double*,
-                                          unsigned, int, cudaStream_t);
+                                          unsigned, int, int, cudaStream_t);
 template cudaError_t launch_panel<float>(float*, int, int, int, int, int*, int*, double*,
-                                         unsigned, int, cudaStream_t);
+                                         unsigned, int, int, cudaStream_t);
 
 }  // namespace gbla

@@ -50,10 +50,27 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.gbla_lu_solve(0, 4, -1, fake, 4, fake, fake, 4, fake, fake, 1 << 20, v) == -3
     assert lib.gbla_lu_factor_mixed(4, fake, 4, fake, 4, fake, fake, 9, 0, fake, 1 << 20, v) == -8
     assert lib.gbla_backward_error(4, 1, fake, 2, fake, 4, fake, 4, fake, fake, 1 << 20, v) == -4
-    opts = _lib.GmresirOpts(1e-14, 1e-8, 10, 500)
+    opts = _lib.GmresirOpts(1e-14, 1e-8, 10, 500, 1)
     st = _lib.GmresirStats()
     assert lib.gbla_gmresir_solve(4, fake, 4, fake, 4, fake, fake, fake, ctypes.byref(opts),
                                   ctypes.byref(st), fake, 1 << 20, v) == -9
+    opts = _lib.GmresirOpts(1e-14, 1e-8, 10, 50, -1)       # negative restart count
+    assert lib.gbla_gmresir_solve(4, fake, 4, fake, 4, fake, fake, fake, ctypes.byref(opts),
+                                  ctypes.byref(st), fake, 1 << 20, v) == -9
+    opts = _lib.GmresirOpts(1e-14, 1e-8, 10, 50, 2)
+    sts = (_lib.GmresirStats * 3)()
+    nrhs = lib.gbla_gmresir_solve_nrhs
+    assert nrhs(4, -1, fake, 4, fake, 4, fake, fake, 4, fake, 4, ctypes.byref(opts), sts, fake,
+                1 << 20, v) == -2
+    assert nrhs(4, 3, fake, 4, fake, 4, fake, fake, 3, fake, 4, ctypes.byref(opts), sts, fake,
+                1 << 20, v) == -9
+    assert nrhs(4, 3, fake, 4, fake, 4, fake, fake, 4, fake, 4, ctypes.byref(opts), None, fake,
+                1 << 20, v) == -13
+    assert nrhs(4, 3, fake, 4, fake, 4, fake, fake, 4, fake, 4, ctypes.byref(opts), sts, v,
+                1 << 20, v) == 1001
+    # no right-hand sides: nothing to do, nothing touched
+    assert nrhs(4, 0, fake, 4, fake, 4, fake, v, 4, v, 4, ctypes.byref(opts), None, fake,
+                1 << 20, v) == 0
 
 
 def test_workspace_sizes(lib):

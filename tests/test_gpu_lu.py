@@ -120,21 +120,34 @@ def test_backward_error_kernel_matches_oracle():
     assert np.abs(beta - beta_o).max() <= 2 * n * 2.0 ** -53
 
 
-def test_wait_timeout_reports_status():
-    """A wait limit of 0 ns makes every cross-CTA wait give up at once; the call must
-    return with GBLA_INFO_TIMEOUT in info, and the context must stay usable."""
-    n = 2048
+@pytest.mark.parametrize("prec,n", [("fp64", 2048), ("fp64", 4224), ("bf16", 1024)])
+def test_wait_timeout_reports_status(prec, n):
+    """A wait limit of 0 ns makes the inter-CTA waits give up at once: the
+    cluster panel (FP64 n = 2048; FP32 in the bf16 case, with the tensor-core
+    update after it), the cooperative panel of rows beyond one cluster (FP64
+    n = 4224). The call must end with GBLA_INFO_TIMEOUT in info and pivots
+    that are all in range; the context must stay usable, and the next
+    factorisation (with the limit restored) must be correct."""
     A = inputs.uniform(n, seed=9).to(DEV)
     old = api.get_wait_timeout_ns()
     try:
         api.set_wait_timeout_ns(0)
-        LU, ipiv, info = api.lu_factor(A, nb=64)
+        if prec == "fp64":
+            LU, ipiv, info = api.lu_factor(A, nb=64)
+        else:
+            LU, ipiv, info = api.lu_factor_mixed(A, prec=prec, nb=128)
         torch.cuda.synchronize()
         v = int(info.item())
+        piv = ipiv.cpu().numpy()
     finally:
         api.set_wait_timeout_ns(old)
     assert v == -1000
-    # the context still works
-    LU, ipiv, info = api.lu_factor(A[:64, :64].contiguous())
-    torch.cuda.synchronize()
-    assert int(info.item()) == 0
+    assert np.all(piv >= np.arange(1, n + 1)) and np.all(piv <= n)
+    # the context still works, and gives the oracle's factorisation
+    m = 300
+    B = inputs.uniform(m, seed=10)
+    LUg, ipg, info_g = _lu_gpu(B, 64)
+    LUo, ipo, _ = oracle.getrf(np.asfortranarray(B.numpy()))
+    assert info_g == 0
+    assert np.array_equal(ipg, ipo)
+    assert np.abs(LUg - LUo).max() <= 1e-11 * np.abs(LUo).max()

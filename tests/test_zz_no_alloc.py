@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
 
 
-def _static_factor(A, nb):
+def _static_factor(A, nb, expect_rc=0):
     n = A.shape[0]
     LU = api.colmajor(A.to(DEV), torch.float64, copy=True)
     ipiv = torch.empty(max(n, 1), dtype=torch.int32, device=DEV)
@@ -24,7 +24,7 @@ def _static_factor(A, nb):
     rc = _lib.load().gbla_lu_factor_static(n, ctypes.c_void_p(LU.data_ptr()), LU.stride(1),
                                            ctypes.c_void_p(ipiv.data_ptr()),
                                            ctypes.c_void_p(info.data_ptr()), nb, stream)
-    assert rc == 0, (rc, _lib.load().gbla_last_error())
+    assert rc == expect_rc, (rc, _lib.load().gbla_last_error())
     torch.cuda.synchronize()
     return LU.cpu().numpy(), ipiv[:n].cpu().numpy(), int(info.item())
 
@@ -48,3 +48,25 @@ def test_static_rejects_bad_arguments():
     assert L.gbla_lu_factor_static(-1, v, 1, v, v, 0, v) == -1
     assert L.gbla_lu_factor_static(8, ctypes.c_void_p(256), 8, ctypes.c_void_p(256),
                                    ctypes.c_void_p(256), 40, v) == -6
+
+
+def test_static_after_a_call_that_gave_up():
+    """The shared array is cleared by every call, so slot words left by a call
+    whose waits gave up part way (wait limit 0: info = GBLA_INFO_TIMEOUT) cannot
+    be mistaken for fresh ones by the next call: it must match gbla_lu_factor."""
+    n, nb = 1000, 128
+    old = api.get_wait_timeout_ns()
+    try:
+        api.set_wait_timeout_ns(0)
+        _, _, info0 = _static_factor(inputs.uniform(n, seed=41), nb)
+    finally:
+        api.set_wait_timeout_ns(old)
+    assert info0 == -1000
+    A = inputs.uniform(n, seed=42)
+    LUs, ips, infos = _static_factor(A, nb)
+    LUw, ipw, infow = api.lu_factor(A.to(DEV), nb=nb)
+    torch.cuda.synchronize()
+    assert infos == int(infow.item()) == 0
+    assert np.array_equal(ips, ipw.cpu().numpy())
+    LUw = LUw.cpu().numpy()
+    assert np.abs(LUs - LUw).max() <= 1e-11 * np.abs(LUw).max()
