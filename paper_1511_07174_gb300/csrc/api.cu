@@ -159,8 +159,11 @@ static bool aligned256(const void* p) { return (reinterpret_cast<uintptr_t>(p) &
 // the trailing update.
 static size_t lu_work_layout(Carver& c, int n, int nb, int prec, LuWork* w) {
   double* slots = c.take<double>(panel_slots_doubles());
+  const size_t li = left_perm_ints(n, nb);
+  int* left = li ? c.take<int>(li) : nullptr;
   if (w) {
     w->slots = slots;
+    w->left = left;
     w->Ak = w->Bk = nullptr;
     w->eA = w->eB = nullptr;
     w->ldk = 0;
@@ -188,6 +191,8 @@ cudaError_t blocked_lu(int n, Ts* A, int lda, int* ipiv, int* info, int nb, int 
                               const LuWork& w, cudaStream_t s) {
   typedef Ts Tc_trsm;  // substitution arithmetic: FP64 for FP64 storage, FP32 for FP32
   unsigned* inner_ctr = reinterpret_cast<unsigned*>(w.slots + kPanelExchangeDoubles);
+  // the columns left of each block get its interchanges at the end when possible
+  const bool defer_left = w.left != nullptr && left_deferred_fits<Ts>(n, nb);
   cudaError_t e;
   for (int k0 = 0; k0 < n; k0 += nb) {
     const int kb = std::min(nb, n - k0);
@@ -215,9 +220,11 @@ cudaError_t blocked_lu(int n, Ts* A, int lda, int* ipiv, int* info, int nb, int 
         if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
       }
     }
-    // the block's interchanges on every column outside it (the U row block
-    // and the trailing update below read the interchanged rows)
-    PROF(KK_LASWP, s, launch_laswp_block<Ts>(A, lda, n, n, k0, kb, ipiv + k0, k0, k0 + kb, s));
+    // the block's interchanges on the columns right of it (the U row block
+    // and the trailing update below read the interchanged rows) and, unless
+    // deferred, on the columns left of it
+    PROF(KK_LASWP, s, launch_laswp_block<Ts>(A, lda, n, n, k0, kb, ipiv + k0, defer_left ? 0 : k0,
+                                             k0 + kb, s));
     if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
     const int nt = n - k0 - kb;
     if (nt <= 0) continue;
@@ -243,6 +250,10 @@ cudaError_t blocked_lu(int n, Ts* A, int lda, int* ipiv, int* info, int nb, int 
                                A + (k0 + kb) + (size_t)(k0 + kb) * lda, lda, false, s));
       if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
     }
+  }
+  if (defer_left) {
+    PROF(KK_LASWP, s, launch_left_interchanges<Ts>(A, lda, n, nb, ipiv, w.left, s));
+    if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
   }
   return cudaSuccess;
 }

@@ -123,6 +123,17 @@ template <typename T>
 cudaError_t launch_laswp_block(T* A, int lda, int ncols, int nrows, int k0, int kb, const int* ipiv,
                                int skip_lo, int skip_hi, cudaStream_t s);
 
+// The interchanges of the columns left of every outer block, applied once
+// after the last block (a permutation gather per column). work:
+// left_perm_ints(n, nb) ints. Possible when left_deferred_fits<T>(n, nb)
+// (a row permutation and a column segment fit in one CTA's shared memory).
+size_t left_perm_ints(int n, int nb);
+template <typename T>
+bool left_deferred_fits(int n, int nb);
+template <typename T>
+cudaError_t launch_left_interchanges(T* A, int lda, int n, int nb, const int* ipiv, int* work,
+                                     cudaStream_t s);
+
 // B (w x N, ldb) <- L^{-1} B with L unit lower (w x w, ldl). Tc: arithmetic type.
 // out_kind: 0 none, GBLA_PREC_BF16/FP16/TF32 -> also write a K-major copy of
 // the result (column j at outK + j*ldk, 2- or 4-byte elements) with one
@@ -231,6 +242,9 @@ cudaError_t launch_chol(int n, double* A, int lda, int* info, cudaStream_t s);
 // ---- blocked LU driver (api.cu) ---------------------------------------------
 struct LuWork {
   double* slots;        // panel exchange slots, panel_slots_doubles(), zeroed per factorisation
+  // left_perm_ints(n, nb) ints: the interchanges left of each outer block are
+  // applied once at the end (nullptr: block by block)
+  int* left = nullptr;
   // mixed path only
   void* Ak;
   void* Bk;

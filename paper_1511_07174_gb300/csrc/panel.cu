@@ -437,6 +437,120 @@ template cudaError_t launch_laswp_block<double>(double*, int, int, int, int, int
 template cudaError_t launch_laswp_block<float>(float*, int, int, int, int, int, const int*, int, int,
                                                cudaStream_t);
 
+// ---------------------------------------------------------------------------
+// Interchanges of the columns left of each outer block, applied once after
+// the last block instead of block by block: a column of block b needs the
+// interchanges of every later block c > b on its rows q >= k_{b+1}. With
+// sigma_c the map "row q receives the old value of row sigma_c(q)" of block
+// c's interchanges (the identity outside the rows they touch), the final value
+// of row q comes from row tau_b(q) = sigma_{b+1}(sigma_{b+2}(...(q))).
+//
+// left_perm_kernel (one CTA): sigma_c is formed by running block c's
+// interchanges, in order, on an identity array in shared memory (one thread);
+// tau is composed from the last block backwards, tau <- sigma_c o tau, and
+// tau_{c-1} is stored for every block c >= 1 (rows >= k_c; the rest of the
+// row range is not read). Pivots outside [row, n) are ignored, as everywhere.
+__global__ void __launch_bounds__(1024)
+    left_perm_kernel(int n, int nb, const int* __restrict__ ipiv, int* __restrict__ tau,
+                     int* __restrict__ snaps) {
+  extern __shared__ int lp_D[];  // n entries
+  const int tid = threadIdx.x;
+  for (int q = tid; q < n; q += blockDim.x) {
+    lp_D[q] = q;
+    tau[q] = q;
+  }
+  __syncthreads();
+  const int nblk = (n + nb - 1) / nb;
+  for (int c = nblk - 1; c >= 1; --c) {
+    const int k0 = c * nb, kb = min(nb, n - k0);
+    if (tid == 0) {
+      for (int j = 0; j < kb; ++j) {
+        int p = ipiv[k0 + j] - 1;
+        if (p < k0 + j || p >= n) p = k0 + j;
+        const int t = lp_D[k0 + j];
+        lp_D[k0 + j] = lp_D[p];
+        lp_D[p] = t;
+      }
+    }
+    __syncthreads();
+    int* snap = snaps + (size_t)(c - 1) * n;
+    for (int q = k0 + tid; q < n; q += blockDim.x) {
+      const int v = lp_D[tau[q]];
+      tau[q] = v;
+      snap[q] = v;
+    }
+    __syncthreads();
+    // back to the identity on the rows block c touched
+    for (int j = tid; j < kb; j += blockDim.x) {
+      int p = ipiv[k0 + j] - 1;
+      if (p < k0 + j || p >= n) p = k0 + j;
+      lp_D[k0 + j] = k0 + j;
+      lp_D[p] = p;
+    }
+    __syncthreads();
+  }
+}
+
+// left_gather_kernel: CTA x = column x of blocks 0 .. nblk-2; rows
+// [k_{b+1}, n) of the column are staged in shared memory and written back
+// through tau_b (coalesced loads and stores).
+template <typename T>
+__global__ void __launch_bounds__(256)
+    left_gather_kernel(T* __restrict__ A, int lda, int n, int nb, const int* __restrict__ snaps) {
+  extern __shared__ double lg_smem[];
+  T* seg = reinterpret_cast<T*>(lg_smem);
+  const int col = blockIdx.x;
+  const int b = col / nb;
+  const int r0 = (b + 1) * nb;
+  const int len = n - r0;
+  if (len <= 0) return;
+  T* a = A + (size_t)col * lda + r0;
+  const int* tb = snaps + (size_t)b * n + r0;
+  for (int i = threadIdx.x; i < len; i += blockDim.x) seg[i] = a[i];
+  __syncthreads();
+  for (int i = threadIdx.x; i < len; i += blockDim.x) a[i] = seg[tb[i] - r0];
+}
+
+size_t left_perm_ints(int n, int nb) {
+  const int nblk = (n + nb - 1) / nb;
+  return nblk >= 2 ? (size_t)n * (size_t)nblk : 0;  // tau + (nblk - 1) snapshots
+}
+
+template <typename T>
+bool left_deferred_fits(int n, int nb) {
+  const DeviceProps& dp = device_props();
+  return (size_t)n * sizeof(int) <= dp.smem_optin && (size_t)n * sizeof(T) <= dp.smem_optin &&
+         n > nb;
+}
+template bool left_deferred_fits<double>(int, int);
+template bool left_deferred_fits<float>(int, int);
+
+template <typename T>
+cudaError_t launch_left_interchanges(T* A, int lda, int n, int nb, const int* ipiv, int* work,
+                                     cudaStream_t s) {
+  const int nblk = (n + nb - 1) / nb;
+  if (nblk < 2) return cudaSuccess;
+  int* tau = work;
+  int* snaps = work + n;
+  const size_t sm_d = (size_t)n * sizeof(int);
+  cudaError_t e = ensure_dyn_smem(left_perm_kernel, sm_d);
+  if (e != cudaSuccess) return e;
+  left_perm_kernel<<<1, 1024, sm_d, s>>>(n, nb, ipiv, tau, snaps);
+  count_launch();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t sm_g = (size_t)(n - nb) * sizeof(T);
+  e = ensure_dyn_smem(left_gather_kernel<T>, sm_g);
+  if (e != cudaSuccess) return e;
+  left_gather_kernel<T><<<(nblk - 1) * nb, 256, sm_g, s>>>(A, lda, n, nb, snaps);
+  count_launch();
+  return cudaGetLastError();
+}
+template cudaError_t launch_left_interchanges<double>(double*, int, int, int, const int*, int*,
+                                                      cudaStream_t);
+template cudaError_t launch_left_interchanges<float>(float*, int, int, int, const int*, int*,
+                                                     cudaStream_t);
+
 // The exchange area holds two parities of slots for up to kPanelMaxSms CTAs;
 // the launcher never uses more CTAs than that.
 static_assert(kPanelExchangeDoubles == (size_t)2 * (kPanelMaxSms + 1) * kPanelSlotW,
