@@ -263,6 +263,35 @@ int gbla_lu_solve_batched_f32(int batch, const int *d_n, float *const *d_A, cons
                               int threads, int ctas_per_sm, void *d_work, size_t work_bytes,
                               gbla_stream_t stream);
 
+/*
+ * The batched LU split in two, so that the factors serve later right-hand
+ * sides (the same persistent launch structure, no host synchronisation, no
+ * allocation, graph-capturable; the same workspace, gbla_lu_batched_workspace):
+ * gbla_lu_factor_batched[_f32]: factor only -- d_A overwritten by L\U, d_ipiv
+ *   and d_info written, as by gbla_lu_solve_batched with d_nrhs = NULL.
+ * gbla_lu_solve_factored_batched[_f32]: B <- U^{-1} L^{-1} P B for every
+ *   system from the factors (d_LU) and pivots (d_ipiv) of a factor-only call,
+ *   which are only read; d_nrhs (0..4 each) must be given. No info.
+ */
+int gbla_lu_factor_batched(int batch, const int *d_n, double *const *d_A, const int *d_lda,
+                           int *const *d_ipiv, int *d_info, const int *d_order, int max_n,
+                           int threads, int ctas_per_sm, void *d_work, size_t work_bytes,
+                           gbla_stream_t stream);
+int gbla_lu_factor_batched_f32(int batch, const int *d_n, float *const *d_A, const int *d_lda,
+                               int *const *d_ipiv, int *d_info, const int *d_order, int max_n,
+                               int threads, int ctas_per_sm, void *d_work, size_t work_bytes,
+                               gbla_stream_t stream);
+int gbla_lu_solve_factored_batched(int batch, const int *d_n, double *const *d_LU,
+                                   const int *d_lda, int *const *d_ipiv, const int *d_nrhs,
+                                   double *const *d_B, const int *d_ldb, const int *d_order,
+                                   int max_n, int threads, int ctas_per_sm, void *d_work,
+                                   size_t work_bytes, gbla_stream_t stream);
+int gbla_lu_solve_factored_batched_f32(int batch, const int *d_n, float *const *d_LU,
+                                       const int *d_lda, int *const *d_ipiv, const int *d_nrhs,
+                                       float *const *d_B, const int *d_ldb, const int *d_order,
+                                       int max_n, int threads, int ctas_per_sm, void *d_work,
+                                       size_t work_bytes, gbla_stream_t stream);
+
 /* ------------------------------------------------------------------------
  * Batched Cholesky + solve (step a9 for symmetric positive definite systems:
  * A = L L^t and the two substitutions of paper section 2, for every system of
@@ -286,6 +315,30 @@ int gbla_chol_solve_batched_f32(int batch, const int *d_n, float *const *d_A, co
                                 const int *d_nrhs, float *const *d_B, const int *d_ldb, int *d_info,
                                 const int *d_order, int max_n, int threads, int ctas_per_sm,
                                 void *d_work, size_t work_bytes, gbla_stream_t stream);
+
+/* The batched Cholesky split in two (as the LU above; workspace
+ * gbla_chol_batched_workspace): gbla_chol_factor_batched[_f32] factors only
+ * (lower triangles overwritten by L, d_info written);
+ * gbla_chol_solve_factored_batched[_f32] solves L y = b, L^t x = y for every
+ * system from those factors (only read), d_nrhs given, no info. */
+int gbla_chol_factor_batched(int batch, const int *d_n, double *const *d_A, const int *d_lda,
+                             int *d_info, const int *d_order, int max_n, int threads,
+                             int ctas_per_sm, void *d_work, size_t work_bytes,
+                             gbla_stream_t stream);
+int gbla_chol_factor_batched_f32(int batch, const int *d_n, float *const *d_A, const int *d_lda,
+                                 int *d_info, const int *d_order, int max_n, int threads,
+                                 int ctas_per_sm, void *d_work, size_t work_bytes,
+                                 gbla_stream_t stream);
+int gbla_chol_solve_factored_batched(int batch, const int *d_n, double *const *d_L,
+                                     const int *d_lda, const int *d_nrhs, double *const *d_B,
+                                     const int *d_ldb, const int *d_order, int max_n, int threads,
+                                     int ctas_per_sm, void *d_work, size_t work_bytes,
+                                     gbla_stream_t stream);
+int gbla_chol_solve_factored_batched_f32(int batch, const int *d_n, float *const *d_L,
+                                         const int *d_lda, const int *d_nrhs, float *const *d_B,
+                                         const int *d_ldb, const int *d_order, int max_n,
+                                         int threads, int ctas_per_sm, void *d_work,
+                                         size_t work_bytes, gbla_stream_t stream);
 
 /*
  * Rank-k product C = alpha * U V^t + beta * C (FP64; U m x k, V n x k, C m x n;

@@ -62,6 +62,14 @@ _SIGS = {
     "gbla_lu_batched_workspace": ([_i], _sz),
     "gbla_lu_solve_batched": ([_i] + [_vp] * 9 + [_i, _i, _i, _vp, _sz, _vp], _i),
     "gbla_lu_solve_batched_f32": ([_i] + [_vp] * 9 + [_i, _i, _i, _vp, _sz, _vp], _i),
+    "gbla_lu_factor_batched": ([_i] + [_vp] * 6 + [_i, _i, _i, _vp, _sz, _vp], _i),
+    "gbla_lu_factor_batched_f32": ([_i] + [_vp] * 6 + [_i, _i, _i, _vp, _sz, _vp], _i),
+    "gbla_lu_solve_factored_batched": ([_i] + [_vp] * 8 + [_i, _i, _i, _vp, _sz, _vp], _i),
+    "gbla_lu_solve_factored_batched_f32": ([_i] + [_vp] * 8 + [_i, _i, _i, _vp, _sz, _vp], _i),
+    "gbla_chol_factor_batched": ([_i] + [_vp] * 5 + [_i, _i, _i, _vp, _sz, _vp], _i),
+    "gbla_chol_factor_batched_f32": ([_i] + [_vp] * 5 + [_i, _i, _i, _vp, _sz, _vp], _i),
+    "gbla_chol_solve_factored_batched": ([_i] + [_vp] * 7 + [_i, _i, _i, _vp, _sz, _vp], _i),
+    "gbla_chol_solve_factored_batched_f32": ([_i] + [_vp] * 7 + [_i, _i, _i, _vp, _sz, _vp], _i),
     "gbla_chol_batched_workspace": ([_i], _sz),
     "gbla_chol_solve_batched": ([_i] + [_vp] * 8 + [_i, _i, _i, _vp, _sz, _vp], _i),
     "gbla_chol_solve_batched_f32": ([_i] + [_vp] * 8 + [_i, _i, _i, _vp, _sz, _vp], _i),

@@ -125,6 +125,50 @@ class BatchedLU:
             _check("gbla_chol_solve_batched",
                    fn(self.batch, p(self.d_n), p(self.d_A), p(self.d_lda), *rhs, *tail))
 
+    def factor(self):
+        """Factor every system (factor-only launch): the work buffers hold the
+        factors and pivots afterwards, as after run() without right-hand sides."""
+        L = _lib.load()
+        p = lambda x: ctypes.c_void_p(x.data_ptr()) if x is not None else ctypes.c_void_p(0)
+        tail = (p(self.info), p(self.d_order), self.max_n, self.threads, self.ctas_per_sm, p(self.ws),
+                self.ws.numel(), _stream())
+        f64 = self.dtype == torch.float64
+        if self.method == "lu":
+            fn = L.gbla_lu_factor_batched if f64 else L.gbla_lu_factor_batched_f32
+            _check("gbla_lu_factor_batched", fn(self.batch, p(self.d_n), p(self.d_A), p(self.d_lda),
+                                                p(self.d_ipiv), *tail))
+        else:
+            fn = L.gbla_chol_factor_batched if f64 else L.gbla_chol_factor_batched_f32
+            _check("gbla_chol_factor_batched", fn(self.batch, p(self.d_n), p(self.d_A), p(self.d_lda),
+                                                  *tail))
+
+    def solve(self, Bs=None):
+        """Solve with the factors of an earlier factor() (solve-only launch). Bs: new
+        right-hand sides with the same shapes as the constructor's (default: those)."""
+        if self.nrhs is None:
+            raise ValueError("no right-hand sides")
+        if Bs is None:
+            self.B.copy_(self.B0)
+        else:
+            flat = torch.cat([(B if B.dim() == 2 else B.unsqueeze(1)).t().reshape(-1).to(self.dtype)
+                              for B in Bs])
+            self.B[:flat.numel()].copy_(flat)
+        L = _lib.load()
+        p = lambda x: ctypes.c_void_p(x.data_ptr())
+        tail = (p(self.d_order), self.max_n, self.threads, self.ctas_per_sm, p(self.ws), self.ws.numel(),
+                _stream())
+        f64 = self.dtype == torch.float64
+        if self.method == "lu":
+            fn = L.gbla_lu_solve_factored_batched if f64 else L.gbla_lu_solve_factored_batched_f32
+            _check("gbla_lu_solve_factored_batched",
+                   fn(self.batch, p(self.d_n), p(self.d_A), p(self.d_lda), p(self.d_ipiv), p(self.d_nrhs),
+                      p(self.d_B), p(self.d_ldb), *tail))
+        else:
+            fn = L.gbla_chol_solve_factored_batched if f64 else L.gbla_chol_solve_factored_batched_f32
+            _check("gbla_chol_solve_factored_batched",
+                   fn(self.batch, p(self.d_n), p(self.d_A), p(self.d_lda), p(self.d_nrhs), p(self.d_B),
+                      p(self.d_ldb), *tail))
+
     def capture(self):
         """Record restore + run as a CUDA graph (after one eager run, so that every
         one-time set-up has happened)."""

@@ -511,7 +511,7 @@ template <typename T>
 static int lu_batched_entry(int batch, const int* d_n, T* const* d_A, const int* d_lda,
                             int* const* d_ipiv, const int* d_nrhs, T* const* d_B, const int* d_ldb,
                             int* d_info, const int* d_order, int max_n, int threads, int ctas_per_sm,
-                            void* d_work, size_t work_bytes, gbla_stream_t stream) {
+                            void* d_work, size_t work_bytes, gbla_stream_t stream, bool solve_only) {
   clear_error();
   if (batch < 0) return -1;
   if (batch > 0 && !d_n) return -2;
@@ -519,6 +519,7 @@ static int lu_batched_entry(int batch, const int* d_n, T* const* d_A, const int*
   if (batch > 0 && !d_lda) return -4;
   if (batch > 0 && !d_ipiv) return -5;
   if (d_nrhs && (!d_B || !d_ldb)) return -7;
+  if (solve_only && batch > 0 && !d_nrhs) return -6;
   if (max_n < 0) return -11;
   if (threads != 0 && (threads % 32 != 0 || threads < 32 || threads > 1024)) return -12;
   if (ctas_per_sm < 0 || ctas_per_sm > 32) return -13;
@@ -529,7 +530,7 @@ static int lu_batched_entry(int batch, const int* d_n, T* const* d_A, const int*
   if (!c.ok) return GBLA_ERR_WORKSPACE;
   if (batch == 0) return GBLA_OK;
   GBLA_TRYK(KK_BATCHED, s, launch_lu_batched<T>(batch, d_n, d_A, d_lda, d_ipiv, d_nrhs, d_B, d_ldb, d_info,
-                                              d_order, max_n, threads, ctas_per_sm, counter, s));
+                                              d_order, max_n, threads, ctas_per_sm, counter, solve_only, s));
   return GBLA_OK;
 }
 
@@ -540,7 +541,7 @@ int gbla_lu_solve_batched(int batch, const int* d_n, double* const* d_A, const i
                           int* d_info, const int* d_order, int max_n, int threads, int ctas_per_sm,
                           void* d_work, size_t work_bytes, gbla_stream_t stream) {
   return lu_batched_entry<double>(batch, d_n, d_A, d_lda, d_ipiv, d_nrhs, d_B, d_ldb, d_info, d_order,
-                                  max_n, threads, ctas_per_sm, d_work, work_bytes, stream);
+                                  max_n, threads, ctas_per_sm, d_work, work_bytes, stream, false);
 }
 
 int gbla_lu_solve_batched_f32(int batch, const int* d_n, float* const* d_A, const int* d_lda,
@@ -548,7 +549,40 @@ int gbla_lu_solve_batched_f32(int batch, const int* d_n, float* const* d_A, cons
                               const int* d_ldb, int* d_info, const int* d_order, int max_n, int threads,
                               int ctas_per_sm, void* d_work, size_t work_bytes, gbla_stream_t stream) {
   return lu_batched_entry<float>(batch, d_n, d_A, d_lda, d_ipiv, d_nrhs, d_B, d_ldb, d_info, d_order,
-                                 max_n, threads, ctas_per_sm, d_work, work_bytes, stream);
+                                 max_n, threads, ctas_per_sm, d_work, work_bytes, stream, false);
+}
+
+int gbla_lu_factor_batched(int batch, const int* d_n, double* const* d_A, const int* d_lda,
+                           int* const* d_ipiv, int* d_info, const int* d_order, int max_n, int threads,
+                           int ctas_per_sm, void* d_work, size_t work_bytes, gbla_stream_t stream) {
+  return lu_batched_entry<double>(batch, d_n, d_A, d_lda, d_ipiv, nullptr, nullptr, nullptr, d_info,
+                                  d_order, max_n, threads, ctas_per_sm, d_work, work_bytes, stream, false);
+}
+
+int gbla_lu_factor_batched_f32(int batch, const int* d_n, float* const* d_A, const int* d_lda,
+                               int* const* d_ipiv, int* d_info, const int* d_order, int max_n,
+                               int threads, int ctas_per_sm, void* d_work, size_t work_bytes,
+                               gbla_stream_t stream) {
+  return lu_batched_entry<float>(batch, d_n, d_A, d_lda, d_ipiv, nullptr, nullptr, nullptr, d_info,
+                                 d_order, max_n, threads, ctas_per_sm, d_work, work_bytes, stream, false);
+}
+
+int gbla_lu_solve_factored_batched(int batch, const int* d_n, double* const* d_LU, const int* d_lda,
+                                   int* const* d_ipiv, const int* d_nrhs, double* const* d_B,
+                                   const int* d_ldb, const int* d_order, int max_n, int threads,
+                                   int ctas_per_sm, void* d_work, size_t work_bytes,
+                                   gbla_stream_t stream) {
+  return lu_batched_entry<double>(batch, d_n, d_LU, d_lda, d_ipiv, d_nrhs, d_B, d_ldb, nullptr, d_order,
+                                  max_n, threads, ctas_per_sm, d_work, work_bytes, stream, true);
+}
+
+int gbla_lu_solve_factored_batched_f32(int batch, const int* d_n, float* const* d_LU, const int* d_lda,
+                                       int* const* d_ipiv, const int* d_nrhs, float* const* d_B,
+                                       const int* d_ldb, const int* d_order, int max_n, int threads,
+                                       int ctas_per_sm, void* d_work, size_t work_bytes,
+                                       gbla_stream_t stream) {
+  return lu_batched_entry<float>(batch, d_n, d_LU, d_lda, d_ipiv, d_nrhs, d_B, d_ldb, nullptr, d_order,
+                                 max_n, threads, ctas_per_sm, d_work, work_bytes, stream, true);
 }
 
 }  // extern "C"
@@ -557,13 +591,14 @@ template <typename T>
 static int chol_batched_entry(int batch, const int* d_n, T* const* d_A, const int* d_lda,
                               const int* d_nrhs, T* const* d_B, const int* d_ldb, int* d_info,
                               const int* d_order, int max_n, int threads, int ctas_per_sm,
-                              void* d_work, size_t work_bytes, gbla_stream_t stream) {
+                              void* d_work, size_t work_bytes, gbla_stream_t stream, bool solve_only) {
   clear_error();
   if (batch < 0) return -1;
   if (batch > 0 && !d_n) return -2;
   if (batch > 0 && !d_A) return -3;
   if (batch > 0 && !d_lda) return -4;
   if (d_nrhs && (!d_B || !d_ldb)) return -6;
+  if (solve_only && batch > 0 && !d_nrhs) return -5;
   if (max_n < 0) return -10;
   if (threads != 0 && (threads % 32 != 0 || threads < 32 || threads > 1024)) return -11;
   if (ctas_per_sm < 0 || ctas_per_sm > 32) return -12;
@@ -574,7 +609,8 @@ static int chol_batched_entry(int batch, const int* d_n, T* const* d_A, const in
   if (!c.ok) return GBLA_ERR_WORKSPACE;
   if (batch == 0) return GBLA_OK;
   GBLA_TRYK(KK_BATCHED, s, launch_chol_batched<T>(batch, d_n, d_A, d_lda, d_nrhs, d_B, d_ldb, d_info,
-                                                d_order, max_n, threads, ctas_per_sm, counter, s));
+                                                d_order, max_n, threads, ctas_per_sm, counter,
+                                                solve_only, s));
   return GBLA_OK;
 }
 
@@ -587,7 +623,7 @@ int gbla_chol_solve_batched(int batch, const int* d_n, double* const* d_A, const
                             const int* d_order, int max_n, int threads, int ctas_per_sm,
                             void* d_work, size_t work_bytes, gbla_stream_t stream) {
   return chol_batched_entry<double>(batch, d_n, d_A, d_lda, d_nrhs, d_B, d_ldb, d_info, d_order,
-                                    max_n, threads, ctas_per_sm, d_work, work_bytes, stream);
+                                    max_n, threads, ctas_per_sm, d_work, work_bytes, stream, false);
 }
 
 int gbla_chol_solve_batched_f32(int batch, const int* d_n, float* const* d_A, const int* d_lda,
@@ -595,7 +631,38 @@ int gbla_chol_solve_batched_f32(int batch, const int* d_n, float* const* d_A, co
                                 const int* d_order, int max_n, int threads, int ctas_per_sm,
                                 void* d_work, size_t work_bytes, gbla_stream_t stream) {
   return chol_batched_entry<float>(batch, d_n, d_A, d_lda, d_nrhs, d_B, d_ldb, d_info, d_order,
-                                   max_n, threads, ctas_per_sm, d_work, work_bytes, stream);
+                                   max_n, threads, ctas_per_sm, d_work, work_bytes, stream, false);
+}
+
+int gbla_chol_factor_batched(int batch, const int* d_n, double* const* d_A, const int* d_lda,
+                             int* d_info, const int* d_order, int max_n, int threads, int ctas_per_sm,
+                             void* d_work, size_t work_bytes, gbla_stream_t stream) {
+  return chol_batched_entry<double>(batch, d_n, d_A, d_lda, nullptr, nullptr, nullptr, d_info, d_order,
+                                    max_n, threads, ctas_per_sm, d_work, work_bytes, stream, false);
+}
+
+int gbla_chol_factor_batched_f32(int batch, const int* d_n, float* const* d_A, const int* d_lda,
+                                 int* d_info, const int* d_order, int max_n, int threads,
+                                 int ctas_per_sm, void* d_work, size_t work_bytes,
+                                 gbla_stream_t stream) {
+  return chol_batched_entry<float>(batch, d_n, d_A, d_lda, nullptr, nullptr, nullptr, d_info, d_order,
+                                   max_n, threads, ctas_per_sm, d_work, work_bytes, stream, false);
+}
+
+int gbla_chol_solve_factored_batched(int batch, const int* d_n, double* const* d_L, const int* d_lda,
+                                     const int* d_nrhs, double* const* d_B, const int* d_ldb,
+                                     const int* d_order, int max_n, int threads, int ctas_per_sm,
+                                     void* d_work, size_t work_bytes, gbla_stream_t stream) {
+  return chol_batched_entry<double>(batch, d_n, d_L, d_lda, d_nrhs, d_B, d_ldb, nullptr, d_order, max_n,
+                                    threads, ctas_per_sm, d_work, work_bytes, stream, true);
+}
+
+int gbla_chol_solve_factored_batched_f32(int batch, const int* d_n, float* const* d_L, const int* d_lda,
+                                         const int* d_nrhs, float* const* d_B, const int* d_ldb,
+                                         const int* d_order, int max_n, int threads, int ctas_per_sm,
+                                         void* d_work, size_t work_bytes, gbla_stream_t stream) {
+  return chol_batched_entry<float>(batch, d_n, d_L, d_lda, d_nrhs, d_B, d_ldb, nullptr, d_order, max_n,
+                                   threads, ctas_per_sm, d_work, work_bytes, stream, true);
 }
 
 // ---------------------------------------------------------------------------

@@ -24,13 +24,15 @@ namespace gbla {
 
 constexpr int kBatchMaxRhs = 4;
 
+// solve_only: the matrices already hold L\U and ipiv the pivots (a previous
+// factor-only launch); only the right-hand sides are solved and written.
 template <typename T>
 __global__ void batched_lu_kernel(int batch, const int* __restrict__ nv, T* const* __restrict__ Av,
                                   const int* __restrict__ ldav, int* const* __restrict__ ipivv,
                                   const int* __restrict__ nrhsv, T* const* __restrict__ Bv,
                                   const int* __restrict__ ldbv, int* __restrict__ infov,
                                   const int* __restrict__ order, unsigned* __restrict__ counter,
-                                  int smem_n) {
+                                  int smem_n, int solve_only) {
   extern __shared__ unsigned char smraw[];
   T* sA = reinterpret_cast<T*>(smraw);                        // smem_n x smem_n (ld = smem_n)
   T* sB = sA + (size_t)smem_n * smem_n;                       // smem_n x kBatchMaxRhs
@@ -63,7 +65,7 @@ __global__ void batched_lu_kernel(int batch, const int* __restrict__ nv, T* cons
       }
     int info = 0;
     __syncthreads();
-    for (int j = 0; j < n; ++j) {
+    for (int j = 0; j < (solve_only ? 0 : n); ++j) {
       // argmax of |a_ij|, i >= j
       double bv = -1.0;
       int bi = INT_MAX;
@@ -106,12 +108,12 @@ __global__ void batched_lu_kernel(int batch, const int* __restrict__ nv, T* cons
       }
       __syncthreads();
     }
-    if (in_smem)
+    if (in_smem && !solve_only)
       for (int e = tid; e < n * n; e += nth) {
         const int r = e % n, c = e / n;
         gA[r + (size_t)c * glda] = sA[r + c * smem_n];
       }
-    if (tid == 0 && infov) infov[sys] = info;
+    if (tid == 0 && infov && !solve_only) infov[sys] = info;
     // solve: B <- U^{-1} L^{-1} P B, right-hand sides staged in shared memory
     if (nrhs > 0) {
       T* gB = Bv[sys];
@@ -130,7 +132,7 @@ __global__ void batched_lu_kernel(int batch, const int* __restrict__ nv, T* cons
       if (tid < nrhs)
         for (int j = 0; j < n; ++j) {
           const int p = piv[j] - 1;
-          if (p != j) {
+          if (p > j && p < n) {  // pivots outside j+1 .. n are no interchange
             const T t = bb[j + (size_t)tid * lbb];
             bb[j + (size_t)tid * lbb] = bb[p + (size_t)tid * lbb];
             bb[p + (size_t)tid * lbb] = t;
@@ -176,7 +178,7 @@ __global__ void batched_chol_kernel(int batch, const int* __restrict__ nv, T* co
                                     const int* __restrict__ ldav, const int* __restrict__ nrhsv,
                                     T* const* __restrict__ Bv, const int* __restrict__ ldbv,
                                     int* __restrict__ infov, const int* __restrict__ order,
-                                    unsigned* __restrict__ counter, int smem_n) {
+                                    unsigned* __restrict__ counter, int smem_n, int solve_only) {
   extern __shared__ unsigned char smraw[];
   T* sA = reinterpret_cast<T*>(smraw);                        // smem_n x smem_n (ld = smem_n)
   T* sB = sA + (size_t)smem_n * smem_n;                       // smem_n x kBatchMaxRhs
@@ -206,7 +208,7 @@ __global__ void batched_chol_kernel(int batch, const int* __restrict__ nv, T* co
     if (tid == 0) s_bad = 0;
     int info = 0;
     __syncthreads();
-    for (int j = 0; j < n; ++j) {
+    for (int j = 0; j < (solve_only ? 0 : n); ++j) {
       if (tid == 0) {
         const T d = a[j + (size_t)j * ld];
         if (!(d > (T)0)) {
@@ -232,12 +234,12 @@ __global__ void batched_chol_kernel(int batch, const int* __restrict__ nv, T* co
       }
       __syncthreads();
     }
-    if (in_smem)
+    if (in_smem && !solve_only)
       for (int e = tid; e < n * n; e += nth) {
         const int r = e % n, c = e / n;
         if (r >= c) gA[r + (size_t)c * glda] = sA[r + c * smem_n];
       }
-    if (tid == 0 && infov) infov[sys] = info;
+    if (tid == 0 && infov && !solve_only) infov[sys] = info;
     if (nrhs > 0 && info == 0) {
       T* gB = Bv[sys];
       const int gldb = ldbv[sys];
@@ -294,7 +296,7 @@ template <typename T>
 cudaError_t launch_lu_batched(int batch, const int* n, T* const* A, const int* lda, int* const* ipiv,
                               const int* nrhs, T* const* B, const int* ldb, int* info,
                               const int* order, int max_n, int threads, int ctas_per_sm,
-                              unsigned* counter, cudaStream_t s) {
+                              unsigned* counter, bool solve_only, cudaStream_t s) {
   if (batch <= 0) return cudaSuccess;
   const DeviceProps& dp = device_props();
   if (threads <= 0) threads = 256;
@@ -309,7 +311,7 @@ cudaError_t launch_lu_batched(int batch, const int* n, T* const* A, const int* l
   int grid = dp.num_sms * ctas_per_sm;
   if (grid > batch) grid = batch;
   batched_lu_kernel<T><<<grid, threads, smem, s>>>(batch, n, A, lda, ipiv, nrhs, B, ldb, info, order,
-                                                   counter, smem_n);
+                                                   counter, smem_n, solve_only ? 1 : 0);
   count_launch();
   return cudaGetLastError();
 }
@@ -317,7 +319,8 @@ cudaError_t launch_lu_batched(int batch, const int* n, T* const* A, const int* l
 template <typename T>
 cudaError_t launch_chol_batched(int batch, const int* n, T* const* A, const int* lda, const int* nrhs,
                                 T* const* B, const int* ldb, int* info, const int* order, int max_n,
-                                int threads, int ctas_per_sm, unsigned* counter, cudaStream_t s) {
+                                int threads, int ctas_per_sm, unsigned* counter, bool solve_only,
+                                cudaStream_t s) {
   if (batch <= 0) return cudaSuccess;
   const DeviceProps& dp = device_props();
   if (threads <= 0) threads = 256;
@@ -332,23 +335,23 @@ cudaError_t launch_chol_batched(int batch, const int* n, T* const* A, const int*
   int grid = dp.num_sms * ctas_per_sm;
   if (grid > batch) grid = batch;
   batched_chol_kernel<T><<<grid, threads, smem, s>>>(batch, n, A, lda, nrhs, B, ldb, info, order,
-                                                     counter, smem_n);
+                                                     counter, smem_n, solve_only ? 1 : 0);
   count_launch();
   return cudaGetLastError();
 }
 
 template cudaError_t launch_chol_batched<double>(int, const int*, double* const*, const int*, const int*,
                                                  double* const*, const int*, int*, const int*, int, int,
-                                                 int, unsigned*, cudaStream_t);
+                                                 int, unsigned*, bool, cudaStream_t);
 template cudaError_t launch_chol_batched<float>(int, const int*, float* const*, const int*, const int*,
                                                 float* const*, const int*, int*, const int*, int, int,
-                                                int, unsigned*, cudaStream_t);
+                                                int, unsigned*, bool, cudaStream_t);
 
 template cudaError_t launch_lu_batched<double>(int, const int*, double* const*, const int*, int* const*,
                                                const int*, double* const*, const int*, int*, const int*,
-                                               int, int, int, unsigned*, cudaStream_t);
+                                               int, int, int, unsigned*, bool, cudaStream_t);
 template cudaError_t launch_lu_batched<float>(int, const int*, float* const*, const int*, int* const*,
                                               const int*, float* const*, const int*, int*, const int*,
-                                              int, int, int, unsigned*, cudaStream_t);
+                                              int, int, int, unsigned*, bool, cudaStream_t);
 
 }  // namespace gbla

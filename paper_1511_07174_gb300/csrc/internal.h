@@ -225,16 +225,19 @@ cudaError_t launch_rank_k(int m, int n, int k, double alpha, const double* U, in
                           cudaStream_t s);
 
 // ---- batched LU + solve (batched.cu) -----------------------------------------
+// solve_only: A holds the factors (and ipiv the pivots) of an earlier
+// factor-only launch; only the right-hand sides are solved.
 template <typename T>
 cudaError_t launch_lu_batched(int batch, const int* n, T* const* A, const int* lda, int* const* ipiv,
                               const int* nrhs, T* const* B, const int* ldb, int* info,
                               const int* order, int max_n, int threads, int ctas_per_sm,
-                              unsigned* counter, cudaStream_t s);
+                              unsigned* counter, bool solve_only, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_chol_batched(int batch, const int* n, T* const* A, const int* lda, const int* nrhs,
                                 T* const* B, const int* ldb, int* info, const int* order, int max_n,
-                                int threads, int ctas_per_sm, unsigned* counter, cudaStream_t s);
+                                int threads, int ctas_per_sm, unsigned* counter, bool solve_only,
+                                cudaStream_t s);
 
 // ---- Cholesky (chol.cu) ------------------------------------------------------
 cudaError_t launch_chol(int n, double* A, int lda, int* info, cudaStream_t s);
