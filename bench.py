@@ -541,11 +541,12 @@ def secondary(args, pk):
     S = inputs.spd(n, 2, dev)
     Xs = inputs.normal((n, 16), 3, dev)
     Bs = S @ Xs
-    F, info = api.chol_factor(S)
-    ms_c = _event_ms(lambda: api.chol_factor(S))
+    nbc = api.tune_chol_nb(n)
+    F, info = api.chol_factor(S, nb=nbc)
+    ms_c = _event_ms(lambda: api.chol_factor(S, nb=nbc))
     Xc = api.chol_solve(F, Bs)
     tfc = n ** 3 / 3.0 / (ms_c * 1e-3) / 1e12
-    out["chol_n8192_fp64"] = {"factor_ms": ms_c, "tflops": tfc, "frac_of_fp64_dgemm": tfc / fp64_peak,
+    out["chol_n8192_fp64"] = {"nb": nbc, "factor_ms": ms_c, "tflops": tfc, "frac_of_fp64_dgemm": tfc / fp64_peak,
                               "beta_max": float(api.backward_error(S, Xc, Bs).max().item())}
     del S, F, Xc, A, B
     # batched: 4096 systems n_i in [16, 256], 1-4 RHS, one persistent launch in a CUDA graph

@@ -159,12 +159,14 @@ int gbla_lu_solve(int trans, int n, int nrhs, const double *LU, int lda, const i
  * FP64 Cholesky A = L L^t of an SPD matrix (paper section 2; steps a1, a3,
  * a4 for the SPD case). Lower triangle referenced and overwritten with L; the
  * strict upper triangle is neither read nor written. Blocked right-looking
- * with 64-column blocks: diagonal block in shared memory, the block column
- * below it by substitution, the trailing lower triangle by a rank-64 update.
+ * with outer blocks of nb columns (nb in 64..256, a multiple of 64; 0 = 64),
+ * each done in 64-column steps: diagonal block in shared memory, the block
+ * column below it by substitution, the rest of the outer block by a rank-64
+ * update; then the trailing lower triangle by one rank-nb update.
  * No scratch. d_info: 0, or k > 0 when the leading minor of order k is not
  * positive definite (the rest of the factor is then undefined).
  * ------------------------------------------------------------------------ */
-int gbla_chol_factor(int n, double *A, int lda, int *d_info, gbla_stream_t stream);
+int gbla_chol_factor(int n, double *A, int lda, int *d_info, int nb, gbla_stream_t stream);
 
 /* Solve A X = B from gbla_chol_factor: L y = b (forward), L^t x = y (back).
  * B (n x nrhs, ldb) is overwritten by X. */

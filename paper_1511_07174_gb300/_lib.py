@@ -48,7 +48,7 @@ _SIGS = {
     "gbla_lu_factor_static": ([_i, _vp, _i, _vp, _vp, _i, _vp], _i),
     "gbla_lu_solve_workspace": ([_i, _i], _sz),
     "gbla_lu_solve": ([_i, _i, _i, _vp, _i, _vp, _vp, _i, _vp, _vp, _sz, _vp], _i),
-    "gbla_chol_factor": ([_i, _vp, _i, _vp, _vp], _i),
+    "gbla_chol_factor": ([_i, _vp, _i, _vp, _i, _vp], _i),
     "gbla_chol_solve_workspace": ([_i, _i], _sz),
     "gbla_chol_solve": ([_i, _i, _vp, _i, _vp, _i, _vp, _vp, _sz, _vp], _i),
     "gbla_lu_factor_mixed_workspace": ([_i, _i, _i], _sz),

@@ -105,15 +105,16 @@ def lu_solve(LU, ipiv, B, trans=False, info=None):
 
 
 # -------------------------------------------------------------------- Cholesky
-def chol_factor(A):
+def chol_factor(A, nb=0):
     """A = L L^t (FP64, lower). Returns (matrix with L in its lower triangle, info device int32[1]).
-    The strict upper triangle is copied from A and left untouched."""
+    The strict upper triangle is copied from A and left untouched. nb: outer block width
+    (64, 128, 192 or 256; 0 = 64; see tune_chol_nb)."""
     _require_cuda(A)
     L = _lib.load()
     n = A.shape[0]
     F = colmajor(A, torch.float64, copy=True)
     info = torch.zeros(1, dtype=torch.int32, device=A.device)
-    _check("gbla_chol_factor", L.gbla_chol_factor(n, _p(F), _ld(F), _p(info), _stream()))
+    _check("gbla_chol_factor", L.gbla_chol_factor(n, _p(F), _ld(F), _p(info), int(nb), _stream()))
     return F, info
 
 
@@ -310,24 +311,19 @@ def prof_read(kind):
 
 
 # ------------------------------------------------------------------ autotuning
-def tune_lu_nb(n, candidates=(64, 96, 128, 192, 256), device="cuda", use_cache=True, seed=0):
-    """Block size of the FP64 LU for order n, by timing each candidate on a
-    uniform random matrix of that order; remembered per GPU and n in the same
-    JSON cache as the batched launch shapes."""
+def _tune_nb(kind, n, candidates, run, device, use_cache):
     from . import batched as _b
-    from . import inputs as _in
-    key = "lu_nb|%s|%d" % (torch.cuda.get_device_name(device), n)
+    key = "%s_nb|%s|%d" % (kind, torch.cuda.get_device_name(device), n)
     cache = _b._load_cache() if use_cache else {}
     if key in cache:
         return cache[key]["nb"]
-    A = _in.uniform(n, seed, device)
     res = {}
     for nb in candidates:
-        lu_factor(A, nb=nb)
+        run(nb)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        lu_factor(A, nb=nb)
+        run(nb)
         e1.record()
         torch.cuda.synchronize()
         res[nb] = e0.elapsed_time(e1)
@@ -336,3 +332,20 @@ def tune_lu_nb(n, candidates=(64, 96, 128, 192, 256), device="cuda", use_cache=T
         cache[key] = {"nb": best, "candidates_ms": {str(k): v for k, v in res.items()}}
         _b._store_cache(cache)
     return best
+
+
+def tune_lu_nb(n, candidates=(64, 96, 128, 192, 256), device="cuda", use_cache=True, seed=0):
+    """Block size of the FP64 LU for order n, by timing each candidate on a
+    uniform random matrix of that order; remembered per GPU and n in the same
+    JSON cache as the batched launch shapes."""
+    from . import inputs as _in
+    A = _in.uniform(n, seed, device)
+    return _tune_nb("lu", n, candidates, lambda nb: lu_factor(A, nb=nb), device, use_cache)
+
+
+def tune_chol_nb(n, candidates=(64, 128, 192, 256), device="cuda", use_cache=True, seed=2):
+    """Outer block width of the FP64 Cholesky for order n, timed on an SPD matrix
+    B B^t / n + I of that order; cached like tune_lu_nb."""
+    from . import inputs as _in
+    S = _in.spd(n, seed, device)
+    return _tune_nb("chol", n, candidates, lambda nb: chol_factor(S, nb=nb), device, use_cache)

@@ -456,16 +456,17 @@ int gbla_lu_solve(int trans, int n, int nrhs, const double* LU, int lda, const i
 }
 
 // ---------------------------------------------------------------------------
-int gbla_chol_factor(int n, double* A, int lda, int* d_info, gbla_stream_t stream) {
+int gbla_chol_factor(int n, double* A, int lda, int* d_info, int nb, gbla_stream_t stream) {
   clear_error();
   if (n < 0) return -1;
   if (n > 0 && !A) return -2;
   if (lda < std::max(1, n)) return -3;
   if (!d_info) return -4;
+  if (nb != 0 && (nb % 64 != 0 || nb < 64 || nb > 256)) return -5;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   GBLA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), s));
   if (n == 0) return GBLA_OK;
-  return cuda_status(launch_chol(n, A, lda, d_info, s));
+  return cuda_status(launch_chol(n, A, lda, nb, d_info, s));
 }
 
 size_t gbla_chol_solve_workspace(int n, int nrhs) {

@@ -1,5 +1,6 @@
 // Cholesky factorisation A = L L^t of an SPD matrix (paper section 2), lower
-// triangle, blocked right-looking with 64-column blocks:
+// triangle, blocked right-looking: outer blocks of nb columns (64 .. 256,
+// autotunable), each processed in 64-column steps:
 //   potf2   -- the 64 x 64 diagonal block factored by one CTA in shared memory
 //              (column by column: d = a_jj, stop with info = j + 1 if d <= 0,
 //              l_jj = sqrt(d), l_ij = a_ij / l_jj, a_ik -= l_ij l_kj);
@@ -8,7 +9,9 @@
 //              in shared memory; the second half first receives the update
 //              from the first);
 //   update  -- A22 -= L21 L21^t on the lower triangle (the SIMT GEMM with its
-//              lower-triangle mask; tiles above the diagonal are skipped).
+//              lower-triangle mask; tiles above the diagonal are skipped):
+//              inside the outer block for its remaining columns, then once
+//              per outer block (rank nb) for the trailing matrix.
 // The strict upper triangle of A is never read or written.
 #include "common.cuh"
 #include "internal.h"
@@ -92,43 +95,67 @@ __global__ void __launch_bounds__(128)
     if (k < kb) B[row + (size_t)k * ldb] = x[k];
 }
 
-cudaError_t launch_chol(int n, double* A, int lda, int* info, cudaStream_t s) {
-  for (int k0 = 0; k0 < n; k0 += kCholNb) {
-    const int kb = n - k0 < kCholNb ? n - k0 : kCholNb;
-    double* A11 = A + k0 + (size_t)k0 * lda;
-    prof_begin(KK_PANEL, s);
-    potf2_kernel<<<1, 256, 0, s>>>(kb, A11, lda, k0, info);
-    count_launch();
-    prof_end(KK_PANEL, s);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    const int m = n - k0 - kb;
-    if (m <= 0) break;
-    double* A21 = A11 + kb;
-    // L21 = A21 L11^{-t} in 32-column halves: solve the first half, update the
-    // second with it, solve the second half
-    for (int h0 = 0; h0 < kb; h0 += kCholTrsmW) {
-      const int hb = kb - h0 < kCholTrsmW ? kb - h0 : kCholTrsmW;
-      if (h0 > 0) {
+// Two-level blocking: outer blocks of nb columns (a multiple of 64, up to
+// 256); inside one, 64-column steps (diagonal block, the rows below it, and
+// the update of the rest of the outer block's columns, lower part); after the
+// outer block, one rank-nb update of the trailing lower triangle.
+cudaError_t launch_chol(int n, double* A, int lda, int nb, int* info, cudaStream_t s) {
+  if (nb <= 0) nb = kCholNb;
+  if (nb % kCholNb != 0 || nb > 256) return cudaErrorInvalidValue;
+  for (int o0 = 0; o0 < n; o0 += nb) {
+    const int ob = n - o0 < nb ? n - o0 : nb;
+    for (int k0 = o0; k0 < o0 + ob; k0 += kCholNb) {
+      const int kb = o0 + ob - k0 < kCholNb ? o0 + ob - k0 : kCholNb;
+      double* A11 = A + k0 + (size_t)k0 * lda;
+      prof_begin(KK_PANEL, s);
+      potf2_kernel<<<1, 256, 0, s>>>(kb, A11, lda, k0, info);
+      count_launch();
+      prof_end(KK_PANEL, s);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      const int m = n - k0 - kb;
+      if (m <= 0) break;
+      double* A21 = A11 + kb;
+      // L21 = A21 L11^{-t} in 32-column halves: solve the first half, update the
+      // second with it, solve the second half
+      for (int h0 = 0; h0 < kb; h0 += kCholTrsmW) {
+        const int hb = kb - h0 < kCholTrsmW ? kb - h0 : kCholTrsmW;
+        if (h0 > 0) {
+          prof_begin(KK_GEMM_SIMT, s);
+          e = launch_gemm_simt<double>(m, hb, h0, -1.0, A21, lda, A11 + h0, lda, true, 1.0,
+                                       A21 + (size_t)h0 * lda, lda, false, s);
+          prof_end(KK_GEMM_SIMT, s);
+          if (e != cudaSuccess) return e;
+        }
+        prof_begin(KK_TRSM, s);
+        chol_trsm_kernel<<<(m + 127) / 128, 128, 0, s>>>(m, hb, A11 + h0 + (size_t)h0 * lda, lda,
+                                                         A21 + (size_t)h0 * lda, lda);
+        count_launch();
+        prof_end(KK_TRSM, s);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+      }
+      // the rest of the outer block's columns (lower part): rows k0 + kb .. n,
+      // columns k0 + kb .. o0 + ob
+      const int nrest = o0 + ob - k0 - kb;
+      if (nrest > 0) {
         prof_begin(KK_GEMM_SIMT, s);
-        e = launch_gemm_simt<double>(m, hb, h0, -1.0, A21, lda, A11 + h0, lda, true, 1.0,
-                                     A21 + (size_t)h0 * lda, lda, false, s);
+        e = launch_gemm_simt<double>(m, nrest, kb, -1.0, A21, lda, A21, lda, true, 1.0,
+                                     A21 + (size_t)kb * lda, lda, true, s);
         prof_end(KK_GEMM_SIMT, s);
         if (e != cudaSuccess) return e;
       }
-      prof_begin(KK_TRSM, s);
-      chol_trsm_kernel<<<(m + 127) / 128, 128, 0, s>>>(m, hb, A11 + h0 + (size_t)h0 * lda, lda,
-                                                       A21 + (size_t)h0 * lda, lda);
-      count_launch();
-      prof_end(KK_TRSM, s);
-      e = cudaGetLastError();
+    }
+    // the trailing lower triangle: rank-ob update with the outer block's L21
+    const int mt = n - o0 - ob;
+    if (mt > 0) {
+      double* L21 = A + (o0 + ob) + (size_t)o0 * lda;
+      prof_begin(KK_GEMM_SIMT, s);
+      cudaError_t e = launch_gemm_simt<double>(mt, mt, ob, -1.0, L21, lda, L21, lda, true, 1.0,
+                                               L21 + (size_t)ob * lda, lda, true, s);
+      prof_end(KK_GEMM_SIMT, s);
       if (e != cudaSuccess) return e;
     }
-    prof_begin(KK_GEMM_SIMT, s);
-    e = launch_gemm_simt<double>(m, m, kb, -1.0, A21, lda, A21, lda, true, 1.0,
-                                 A21 + (size_t)kb * lda, lda, true, s);
-    prof_end(KK_GEMM_SIMT, s);
-    if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }

@@ -240,7 +240,8 @@ cudaError_t launch_chol_batched(int batch, const int* n, T* const* A, const int*
                                 cudaStream_t s);
 
 // ---- Cholesky (chol.cu) ------------------------------------------------------
-cudaError_t launch_chol(int n, double* A, int lda, int* info, cudaStream_t s);
+// nb: outer block width, a multiple of 64 up to 256 (0: 64)
+cudaError_t launch_chol(int n, double* A, int lda, int nb, int* info, cudaStream_t s);
 
 // ---- blocked LU driver (api.cu) ---------------------------------------------
 struct LuWork {

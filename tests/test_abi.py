@@ -50,6 +50,8 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.gbla_lu_solve(0, 4, -1, fake, 4, fake, fake, 4, fake, fake, 1 << 20, v) == -3
     assert lib.gbla_lu_factor_mixed(4, fake, 4, fake, 4, fake, fake, 9, 0, fake, 1 << 20, v) == -8
     assert lib.gbla_backward_error(4, 1, fake, 2, fake, 4, fake, 4, fake, fake, 1 << 20, v) == -4
+    assert lib.gbla_chol_factor(4, fake, 4, fake, 96, v) == -5      # nb not a multiple of 64
+    assert lib.gbla_chol_factor(4, fake, 4, fake, 320, v) == -5
     opts = _lib.GmresirOpts(1e-14, 1e-8, 10, 500, 1)
     st = _lib.GmresirStats()
     assert lib.gbla_gmresir_solve(4, fake, 4, fake, 4, fake, fake, fake, ctypes.byref(opts),
