@@ -239,6 +239,52 @@ int gbla_gmresir_solve_nrhs(int n, int nrhs, const double *A, int lda, const flo
                             void *d_work, size_t work_bytes, gbla_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Standalone Krylov solvers (paper section 2: the non-stationary iterative
+ * methods -- GMRES with Gram-Schmidt orthogonalisation and restarts, and
+ * BiCGSTAB -- next to the direct solvers), FP64 on a dense A (n x n, lda),
+ * with an optional preconditioner M = P^t L U: the FP32 factors F (ldf) and
+ * pivots ipiv of gbla_lu_factor_mixed (both NULL: none). x holds the initial
+ * guess on entry and the iterate on return.
+ * gbla_gmres_solve: restarted GMRES(restart_m), modified Gram-Schmidt,
+ *   Givens rotations, left preconditioning; stops when the least-squares
+ *   residual is <= tol * ||M^{-1} b||_2 (||b||_2 without M) or after max_iter
+ *   Krylov steps.
+ * gbla_bicgstab_solve: BiCGSTAB (van der Vorst's stabilised BiCG) with M
+ *   applied to the search directions (p^ = M^{-1} p, s^ = M^{-1} s); all its
+ *   scalars stay on the device; stops when ||r||_2 <= tol * ||b||_2 (the
+ *   recursively updated r) or after max_iter iterations; a vanishing rho',
+ *   (r~, v) or t with r not yet small is reported as a breakdown.
+ * stats: iterations, converged, breakdown, relres = ||b - A x||_2 / ||b||_2
+ * of the returned x (recomputed). SYNCHRONOUS: one scalar read per step.
+ * Returns 0 when converged, GBLA_ERR_NOT_CONVERGED otherwise, GBLA_ERR_TIMEOUT
+ * when a kernel wait gave up. Workspace: gbla_krylov_workspace(n, restart_m)
+ * (restart_m is ignored by BiCGSTAB but sizes the shared layout).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  double tol;     /* relative residual target */
+  int max_iter;   /* Krylov steps (GMRES) or iterations (BiCGSTAB) */
+  int restart_m;  /* GMRES restart length, 1..128 */
+} gbla_krylov_opts;
+
+typedef struct {
+  int iterations;
+  int converged;
+  int breakdown;
+  int pad;
+  double relres;  /* ||b - A x||_2 / ||b||_2 of the returned x */
+} gbla_krylov_stats;
+
+size_t gbla_krylov_workspace(int n, int restart_m);
+int gbla_gmres_solve(int n, const double *A, int lda, const double *b, double *x, const float *F,
+                     int ldf, const int *ipiv, const gbla_krylov_opts *opts,
+                     gbla_krylov_stats *stats, void *d_work, size_t work_bytes,
+                     gbla_stream_t stream);
+int gbla_bicgstab_solve(int n, const double *A, int lda, const double *b, double *x,
+                        const float *F, int ldf, const int *ipiv, const gbla_krylov_opts *opts,
+                        gbla_krylov_stats *stats, void *d_work, size_t work_bytes,
+                        gbla_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Batched LU with partial pivoting + solve (step a9: the factorisation and
  * the two substitutions of paper section 2 for every system of a batch), in
  * ONE persistent kernel launch: a grid of SMs x ctas_per_sm CTAs pulls system

@@ -152,3 +152,70 @@ def gmres_ir(A, b, apply_minv, tol=1e-14, m=50, tau=1e-8, max_outer=10, restarts
         outer += 1
     return x, {"outer": outer, "inner_total": inner_total, "beta_history": betas,
                "converged": converged}
+
+
+def bicgstab(A, b, tol, max_iter, x0=None, apply_minv=None):
+    """BiCGSTAB (the stabilised BiCG of paper section 2), plain numpy FP64,
+    written from the method's recurrences (van der Vorst's form, with the
+    preconditioner applied to the search directions: p^ = M^{-1} p,
+    s^ = M^{-1} s; no preconditioner when apply_minv is None):
+
+        r = b - A x,  r~ = r,  rho = alpha = omega = 1,  v = p = 0
+        repeat:
+          rho' = (r~, r);  beta = (rho' / rho) (alpha / omega)
+          p = r + beta (p - omega v);  p^ = M^{-1} p;  v = A p^
+          alpha = rho' / (r~, v);  s = r - alpha v
+          s^ = M^{-1} s;  t = A s^;  omega = (t, s) / (t, t)
+          x = x + alpha p^ + omega s^;  r = s - omega t;  rho = rho'
+        until ||r||_2 <= tol ||b||_2 or max_iter iterations.
+
+    When t = A s^ vanishes, x + alpha p^ is taken: it is the solution when
+    s = 0, otherwise the method broke down.
+    Returns (x, info dict: iterations, converged, relres history (index 0 =
+    start), breakdown flag when rho' vanishes or t does with s != 0)."""
+    A = np.asarray(A, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    n = b.shape[0]
+    minv = apply_minv if apply_minv is not None else (lambda v: np.array(v, dtype=np.float64))
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64)
+    r = b - A @ x
+    rt = r.copy()
+    rho = alpha = omega = 1.0
+    v = np.zeros(n)
+    p = np.zeros(n)
+    bnorm = np.linalg.norm(b)
+    hist = [np.linalg.norm(r) / bnorm if bnorm > 0 else 0.0]
+    it = 0
+    breakdown = False
+    converged = hist[0] <= tol
+    while not converged and it < max_iter:
+        rho_new = rt @ r
+        if rho_new == 0.0:
+            breakdown = True
+            break
+        beta = (rho_new / rho) * (alpha / omega)
+        p = r + beta * (p - omega * v)
+        ph = minv(p)
+        v = A @ ph
+        alpha = rho_new / (rt @ v)
+        s = r - alpha * v
+        sh = minv(s)
+        t = A @ sh
+        tt = t @ t
+        if tt == 0.0:
+            # t = 0: s = 0 (x + alpha p^ solves the system) or a breakdown
+            x = x + alpha * ph
+            r = s
+            it += 1
+            hist.append(np.linalg.norm(r) / bnorm)
+            converged = hist[-1] <= tol
+            breakdown = not converged
+            break
+        omega = (t @ s) / tt
+        x = x + alpha * ph + omega * sh
+        r = s - omega * t
+        rho = rho_new
+        it += 1
+        hist.append(np.linalg.norm(r) / bnorm)
+        converged = hist[-1] <= tol
+    return x, {"iterations": it, "converged": converged, "relres": hist, "breakdown": breakdown}

@@ -32,6 +32,15 @@ class GmresirStats(ctypes.Structure):
     _fields_ = [("outer", _i), ("inner", _i), ("converged", _i), ("beta", _d), ("beta0", _d)]
 
 
+class KrylovOpts(ctypes.Structure):
+    _fields_ = [("tol", _d), ("max_iter", _i), ("restart_m", _i)]
+
+
+class KrylovStats(ctypes.Structure):
+    _fields_ = [("iterations", _i), ("converged", _i), ("breakdown", _i), ("pad", _i),
+                ("relres", _d)]
+
+
 _SIGS = {
     "gbla_version": ([], ctypes.c_char_p),
     "gbla_status_string": ([_i], ctypes.c_char_p),
@@ -59,6 +68,11 @@ _SIGS = {
     "gbla_gmresir_solve_nrhs": ([_i, _i, _vp, _i, _vp, _i, _vp, _vp, _i, _vp, _i,
                                  ctypes.POINTER(GmresirOpts), ctypes.POINTER(GmresirStats), _vp, _sz,
                                  _vp], _i),
+    "gbla_krylov_workspace": ([_i, _i], _sz),
+    "gbla_gmres_solve": ([_i, _vp, _i, _vp, _vp, _vp, _i, _vp, ctypes.POINTER(KrylovOpts),
+                          ctypes.POINTER(KrylovStats), _vp, _sz, _vp], _i),
+    "gbla_bicgstab_solve": ([_i, _vp, _i, _vp, _vp, _vp, _i, _vp, ctypes.POINTER(KrylovOpts),
+                             ctypes.POINTER(KrylovStats), _vp, _sz, _vp], _i),
     "gbla_lu_batched_workspace": ([_i], _sz),
     "gbla_lu_solve_batched": ([_i] + [_vp] * 9 + [_i, _i, _i, _vp, _sz, _vp], _i),
     "gbla_lu_solve_batched_f32": ([_i] + [_vp] * 9 + [_i, _i, _i, _vp, _sz, _vp], _i),

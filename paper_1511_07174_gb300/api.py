@@ -204,6 +204,38 @@ def solve_mixed(A, b, prec="bf16", nb=256, **kw):
     return x, st
 
 
+def _krylov(name, A, b, x0, tol, max_iter, restart_m, F, ipiv):
+    _require_cuda(A, b, F, ipiv)
+    L = _lib.load()
+    n = A.shape[0]
+    Ac = colmajor(A, torch.float64)
+    bc = b.reshape(-1).to(torch.float64).contiguous()
+    x = (torch.zeros(max(n, 1), dtype=torch.float64, device=A.device) if x0 is None
+         else x0.reshape(-1).to(torch.float64).clone())
+    Fc = colmajor(F, torch.float32) if F is not None else None
+    opts = _lib.KrylovOpts(tol, max_iter, restart_m)
+    st = _lib.KrylovStats()
+    ws = _ws(L.gbla_krylov_workspace(n, restart_m), A.device)
+    rc = getattr(L, name)(n, _p(Ac), _ld(Ac), _p(bc), _p(x), _p(Fc), _ld(Fc) if Fc is not None else max(1, n),
+                          _p(ipiv), ctypes.byref(opts), ctypes.byref(st), _p(ws), ws.numel(), _stream())
+    if rc not in (0, _lib.GBLA_ERR_NOT_CONVERGED):
+        raise GblaError(name, rc)
+    return x[:n], {"iterations": st.iterations, "converged": bool(st.converged),
+                   "breakdown": bool(st.breakdown), "relres": st.relres}
+
+
+def gmres(A, b, x0=None, tol=1e-10, max_iter=1000, restart_m=50, F=None, ipiv=None):
+    """Restarted GMRES(restart_m) for A x = b (FP64), optionally left-preconditioned by
+    mixed-precision LU factors (F, ipiv from lu_factor_mixed). Returns (x, stats)."""
+    return _krylov("gbla_gmres_solve", A, b, x0, tol, max_iter, restart_m, F, ipiv)
+
+
+def bicgstab(A, b, x0=None, tol=1e-10, max_iter=1000, F=None, ipiv=None):
+    """BiCGSTAB for A x = b (FP64), optionally preconditioned by mixed-precision LU
+    factors (F, ipiv from lu_factor_mixed). Returns (x, stats)."""
+    return _krylov("gbla_bicgstab_solve", A, b, x0, tol, max_iter, 1, F, ipiv)
+
+
 def backward_error(A, X, B):
     """Per-column ||B - A X||_inf / (||A||_inf ||X||_inf) on the device (FP64)."""
     _require_cuda(A, X, B)

@@ -961,4 +961,238 @@ int gbla_gmresir_solve(int n, const double* A, int lda, const float* F, int ldf,
                                  opts, stats, d_work, work_bytes, stream);
 }
 
+
+// ---------------------------------------------------------------------------
+// Standalone GMRES(m) and BiCGSTAB (paper section 2: the library's
+// non-stationary iterative solvers), FP64, with an optional preconditioner
+// M = P^t L U from gbla_lu_factor_mixed (FP32 factors, FP64 arithmetic).
+struct KrylovWork {
+  IrWork ir;        // Krylov basis, Hessenberg, rotations, preconditioner pieces
+  double* rt;       // BiCGSTAB shadow residual
+  double* p;
+  double* v;
+  double* sv;
+  double* t;
+  double* ph;
+  double* sh;
+  double* dpart;    // inner-product partial sums
+  double* scal;     // scalars read by the host
+  BcgState* bcg;
+};
+
+static size_t krylov_layout(Carver& c, int n, int m, KrylovWork* w) {
+  const int nn = std::max(n, 1);
+  KrylovWork t;
+  ir_layout(c, n, m, &t.ir);
+  t.rt = c.take<double>(nn);
+  t.p = c.take<double>(nn);
+  t.v = c.take<double>(nn);
+  t.sv = c.take<double>(nn);
+  t.t = c.take<double>(nn);
+  t.ph = c.take<double>(nn);
+  t.sh = c.take<double>(nn);
+  t.dpart = c.take<double>(dot_part_doubles());
+  t.scal = c.take<double>(4);
+  t.bcg = reinterpret_cast<BcgState*>(c.take<char>(sizeof(BcgState)));
+  if (w) *w = t;
+  return c.off;
+}
+
+size_t gbla_krylov_workspace(int n, int restart_m) {
+  if (n < 0 || restart_m < 1 || restart_m > 128) return 0;
+  Carver c(nullptr, 0);
+  return krylov_layout(c, n, restart_m, nullptr);
+}
+
+static int krylov_args(int n, const double* A, int lda, const double* b, double* x, const float* F,
+                       int ldf, const int* ipiv, const gbla_krylov_opts* opts,
+                       gbla_krylov_stats* stats) {
+  if (n < 0) return -1;
+  if (n > 0 && !A) return -2;
+  if (lda < std::max(1, n)) return -3;
+  if (n > 0 && !b) return -4;
+  if (n > 0 && !x) return -5;
+  if ((F != nullptr) != (ipiv != nullptr)) return -6;
+  if (F && ldf < std::max(1, n)) return -7;
+  if (!opts || !(opts->tol >= 0.0) || opts->max_iter < 0 || opts->restart_m < 1 || opts->restart_m > 128)
+    return -9;
+  if (!stats) return -10;
+  return 0;
+}
+
+// ||b - A x||_2 / ||b||_2 with the device matvec and inner products
+static int krylov_relres(int n, const double* A, int lda, const double* b, const double* x,
+                         const KrylovWork& w, cudaStream_t s, double* relres) {
+  GBLA_TRYK(KK_MATVEC, s, launch_residual(n, 1, A, lda, x, n, b, n, w.ir.r, n, w.ir.part, s));
+  GBLA_TRYK(KK_MATVEC, s, launch_dots(n, 2, w.ir.r, w.ir.r, b, b, w.dpart, w.scal, w.scal + 1, s));
+  double h[2];
+  GBLA_TRY(cudaMemcpyAsync(h, w.scal, sizeof(h), cudaMemcpyDeviceToHost, s));
+  GBLA_TRY(cudaStreamSynchronize(s));
+  *relres = h[1] > 0.0 ? sqrt(h[0] / h[1]) : sqrt(h[0]);
+  return GBLA_OK;
+}
+
+int gbla_gmres_solve(int n, const double* A, int lda, const double* b, double* x, const float* F,
+                     int ldf, const int* ipiv, const gbla_krylov_opts* opts,
+                     gbla_krylov_stats* stats, void* d_work, size_t work_bytes,
+                     gbla_stream_t stream) {
+  clear_error();
+  const int bad = krylov_args(n, A, lda, b, x, F, ldf, ipiv, opts, stats);
+  if (bad) return bad;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!d_work || !aligned256(d_work)) return GBLA_ERR_WORKSPACE;
+  const int m = opts->restart_m;
+  Carver c(d_work, work_bytes);
+  KrylovWork w;
+  krylov_layout(c, n, m, &w);
+  if (!c.ok) return GBLA_ERR_WORKSPACE;
+  memset(stats, 0, sizeof(*stats));
+  if (n == 0) {
+    stats->converged = 1;
+    return GBLA_OK;
+  }
+  const DeviceProps& dp = device_props();
+  if (!dp.coop) return GBLA_ERR_DEVICE;
+  const IrWork& ir = w.ir;
+  const bool pre = F != nullptr;
+  GBLA_TRY(cudaMemsetAsync(ir.info, 0, sizeof(int), s));
+  if (pre) {
+    GBLA_TRYK(KK_PERM, s, launch_ipiv_to_perm(n, ipiv, ir.perm, s));
+    GBLA_TRYK(KK_TRSV, s, launch_diag_inv<float>(true, true, n, F, ldf, ir.DinvL, s));
+    GBLA_TRYK(KK_TRSV, s, launch_diag_inv<float>(false, false, n, F, ldf, ir.DinvU, s));
+    GBLA_TRY(apply_minv(n, F, ldf, ir.perm, ir.DinvL, ir.DinvU, b, ir.z, ir.t1, ir.t2, ir.flags, ir.info, s));
+  }
+  // the stopping norm: ||M^{-1} b||_2 (left preconditioning) or ||b||_2
+  const double* bz = pre ? ir.z : b;
+  GBLA_TRYK(KK_MATVEC, s, launch_dots(n, 1, bz, bz, nullptr, nullptr, w.dpart, w.scal, nullptr, s));
+  double bn2 = 0.0;
+  int rc = read_scalar(&bn2, w.scal, ir.info, s);
+  if (rc != GBLA_OK) return rc;
+  const double bn = sqrt(bn2);
+  int it = 0;
+  bool conv = bn == 0.0;
+  while (!conv) {
+    // r = b - A x; z = M^{-1} r; v_0 = z / ||z||
+    GBLA_TRYK(KK_MATVEC, s, launch_residual(n, 1, A, lda, x, n, b, n, ir.r, n, ir.part, s));
+    const double* z = ir.r;
+    if (pre) {
+      GBLA_TRY(apply_minv(n, F, ldf, ir.perm, ir.DinvL, ir.DinvU, ir.r, ir.z, ir.t1, ir.t2, ir.flags, ir.info, s));
+      z = ir.z;
+    }
+    GBLA_TRYK(KK_MGS, s, launch_mgs_step(n, -1, ir.V, ir.ldv, z, ir.H, m + 1, ir.cs, ir.sn, ir.g, ir.st,
+                             ir.slots, ir.counter, ir.info, s));
+    double beta = 0.0;
+    rc = read_scalar(&beta, ir.st, ir.info, s);
+    if (rc != GBLA_OK) return rc;
+    if (beta <= opts->tol * bn) {
+      conv = true;
+      break;
+    }
+    if (it >= opts->max_iter) break;
+    int k = 0;
+    double res = beta;
+    for (int j = 0; j < m && it < opts->max_iter; ++j) {
+      GBLA_TRYK(KK_MATVEC, s, launch_residual(n, 1, A, lda, ir.V + (size_t)j * ir.ldv, n, nullptr, n, ir.w, n,
+                                              ir.part, s));
+      const double* wv = ir.w;
+      if (pre) {
+        GBLA_TRY(apply_minv(n, F, ldf, ir.perm, ir.DinvL, ir.DinvU, ir.w, ir.r, ir.t1, ir.t2, ir.flags, ir.info, s));
+        wv = ir.r;
+      }
+      GBLA_TRYK(KK_MGS, s, launch_mgs_step(n, j, ir.V, ir.ldv, wv, ir.H, m + 1, ir.cs, ir.sn, ir.g, ir.st,
+                               ir.slots, ir.counter, ir.info, s));
+      rc = read_scalar(&res, ir.st, ir.info, s);
+      if (rc != GBLA_OK) return rc;
+      ++it;
+      k = j + 1;
+      if (res <= opts->tol * bn) break;
+    }
+    GBLA_TRYK(KK_UPDATE, s, launch_gmres_update(n, k, ir.V, ir.ldv, ir.H, m + 1, ir.g, x, s));
+    if (res <= opts->tol * bn) conv = true;
+  }
+  stats->iterations = it;
+  stats->converged = conv ? 1 : 0;
+  rc = krylov_relres(n, A, lda, b, x, w, s, &stats->relres);
+  if (rc != GBLA_OK) return rc;
+  return conv ? GBLA_OK : GBLA_ERR_NOT_CONVERGED;
+}
+
+int gbla_bicgstab_solve(int n, const double* A, int lda, const double* b, double* x, const float* F,
+                        int ldf, const int* ipiv, const gbla_krylov_opts* opts,
+                        gbla_krylov_stats* stats, void* d_work, size_t work_bytes,
+                        gbla_stream_t stream) {
+  clear_error();
+  const int bad = krylov_args(n, A, lda, b, x, F, ldf, ipiv, opts, stats);
+  if (bad) return bad;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!d_work || !aligned256(d_work)) return GBLA_ERR_WORKSPACE;
+  Carver c(d_work, work_bytes);
+  KrylovWork w;
+  krylov_layout(c, n, opts->restart_m, &w);
+  if (!c.ok) return GBLA_ERR_WORKSPACE;
+  memset(stats, 0, sizeof(*stats));
+  if (n == 0) {
+    stats->converged = 1;
+    return GBLA_OK;
+  }
+  const DeviceProps& dp = device_props();
+  if (!dp.coop) return GBLA_ERR_DEVICE;
+  const IrWork& ir = w.ir;
+  const bool pre = F != nullptr;
+  GBLA_TRY(cudaMemsetAsync(ir.info, 0, sizeof(int), s));
+  if (pre) {
+    GBLA_TRYK(KK_PERM, s, launch_ipiv_to_perm(n, ipiv, ir.perm, s));
+    GBLA_TRYK(KK_TRSV, s, launch_diag_inv<float>(true, true, n, F, ldf, ir.DinvL, s));
+    GBLA_TRYK(KK_TRSV, s, launch_diag_inv<float>(false, false, n, F, ldf, ir.DinvU, s));
+  }
+  // r = b - A x, r~ = r, p = v = 0, rho = alpha = omega = 1
+  double* r = ir.r;
+  GBLA_TRYK(KK_MATVEC, s, launch_residual(n, 1, A, lda, x, n, b, n, r, n, ir.part, s));
+  GBLA_TRY(cudaMemcpyAsync(w.rt, r, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+  GBLA_TRY(cudaMemsetAsync(w.p, 0, sizeof(double) * (size_t)n, s));
+  GBLA_TRY(cudaMemsetAsync(w.v, 0, sizeof(double) * (size_t)n, s));
+  GBLA_TRYK(KK_UPDATE, s, launch_bcg_init(w.bcg, s));
+  GBLA_TRYK(KK_MATVEC, s, launch_dots(n, 2, r, r, b, b, w.dpart, &w.bcg->rr, w.scal, s));
+  BcgState h;
+  double bn2 = 0.0;
+  GBLA_TRY(cudaMemcpyAsync(&h, w.bcg, sizeof(h), cudaMemcpyDeviceToHost, s));
+  GBLA_TRY(cudaMemcpyAsync(&bn2, w.scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+  GBLA_TRY(cudaStreamSynchronize(s));
+  const double bn = sqrt(bn2);
+  const double* ph = pre ? w.ph : w.p;
+  const double* sh = pre ? w.sh : w.sv;
+  bool conv = bn == 0.0 || sqrt(h.rr) <= opts->tol * bn;
+  int it = 0, brk = 0;
+  while (!conv && it < opts->max_iter) {
+    GBLA_TRYK(KK_MATVEC, s, launch_dots(n, 1, w.rt, r, nullptr, nullptr, w.dpart, &w.bcg->rho_new, nullptr, s));
+    GBLA_TRYK(KK_UPDATE, s, launch_bcg_p(n, r, w.v, w.p, w.bcg, s));
+    if (pre) GBLA_TRY(apply_minv(n, F, ldf, ir.perm, ir.DinvL, ir.DinvU, w.p, w.ph, ir.t1, ir.t2, ir.flags, ir.info, s));
+    GBLA_TRYK(KK_MATVEC, s, launch_residual(n, 1, A, lda, ph, n, nullptr, n, w.v, n, ir.part, s));
+    GBLA_TRYK(KK_MATVEC, s, launch_dots(n, 1, w.rt, w.v, nullptr, nullptr, w.dpart, &w.bcg->rv, nullptr, s));
+    GBLA_TRYK(KK_UPDATE, s, launch_bcg_s(n, r, w.v, w.sv, w.bcg, s));
+    if (pre) GBLA_TRY(apply_minv(n, F, ldf, ir.perm, ir.DinvL, ir.DinvU, w.sv, w.sh, ir.t1, ir.t2, ir.flags, ir.info, s));
+    GBLA_TRYK(KK_MATVEC, s, launch_residual(n, 1, A, lda, sh, n, nullptr, n, w.t, n, ir.part, s));
+    GBLA_TRYK(KK_MATVEC, s, launch_dots(n, 2, w.t, w.sv, w.t, w.t, w.dpart, &w.bcg->ts, &w.bcg->tt, s));
+    GBLA_TRYK(KK_UPDATE, s, launch_bcg_xr(n, x, ph, sh, w.sv, w.t, r, w.bcg, s));
+    GBLA_TRYK(KK_MATVEC, s, launch_dots(n, 1, r, r, nullptr, nullptr, w.dpart, &w.bcg->rr, nullptr, s));
+    int info = 0;
+    GBLA_TRY(cudaMemcpyAsync(&h, w.bcg, sizeof(h), cudaMemcpyDeviceToHost, s));
+    GBLA_TRY(cudaMemcpyAsync(&info, ir.info, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GBLA_TRY(cudaStreamSynchronize(s));
+    if (info == GBLA_INFO_TIMEOUT) return GBLA_ERR_TIMEOUT;
+    ++it;
+    conv = sqrt(h.rr) <= opts->tol * bn;
+    if (!conv && h.status) {
+      brk = 1;  // rho', (r~, v) or t vanished without the residual being small
+      break;
+    }
+  }
+  stats->iterations = it;
+  stats->converged = conv ? 1 : 0;
+  stats->breakdown = brk;
+  int rc = krylov_relres(n, A, lda, b, x, w, s, &stats->relres);
+  if (rc != GBLA_OK) return rc;
+  return conv ? GBLA_OK : GBLA_ERR_NOT_CONVERGED;
+}
+
 }  // extern "C"

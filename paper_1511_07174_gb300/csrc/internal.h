@@ -219,6 +219,26 @@ cudaError_t launch_axpby(int n, double a, const double* x, double b, const doubl
 cudaError_t launch_gmres_update(int n, int k, const double* V, int ldv, const double* H, int ldh,
                                 const double* g, double* x, cudaStream_t s);
 
+// ---- standalone Krylov solvers (iterative.cu) --------------------------------
+// out0 = (x0, y0) [, out1 = (x1, y1)] for K = 1 [2]; fixed summation order.
+size_t dot_part_doubles();
+cudaError_t launch_dots(int n, int K, const double* x0, const double* y0, const double* x1,
+                        const double* y1, double* part, double* out0, double* out1,
+                        cudaStream_t s);
+// Scalars of the BiCGSTAB recurrence, kept on the device.
+struct BcgState {
+  double rho, rho_new, alpha, omega, rv, ts, tt, rr;
+  int status;  // 0, 1 = breakdown (rho' or (r~, v) vanished), 2 = t vanished
+  int pad;
+};
+cudaError_t launch_bcg_init(BcgState* st, cudaStream_t s);
+cudaError_t launch_bcg_p(int n, const double* r, const double* v, double* p, const BcgState* st,
+                         cudaStream_t s);
+cudaError_t launch_bcg_s(int n, const double* r, const double* v, double* sv, BcgState* st,
+                         cudaStream_t s);
+cudaError_t launch_bcg_xr(int n, double* x, const double* ph, const double* sh, const double* sv,
+                          const double* t, double* r, BcgState* st, cudaStream_t s);
+
 // C = alpha * U V^t + beta * C (FP64; any k, in passes of 16)
 cudaError_t launch_rank_k(int m, int n, int k, double alpha, const double* U, int ldu,
                           const double* V, int ldv, double beta, double* C, int ldc,

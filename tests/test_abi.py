@@ -104,3 +104,26 @@ def test_batched_arguments_rejected_on_host(lib):
     assert lib.gbla_chol_solve_batched(0, v, v, v, v, v, v, v, v, 0, 0, 0, fake, ws, v) == 0
     assert lib.gbla_lu_solve_batched(-1, v, v, v, v, v, v, v, v, v, 0, 0, 0, fake, ws, v) == -1
     assert lib.gbla_lu_solve_batched(2, fake, fake, fake, v, v, v, v, v, v, 0, 0, 0, fake, ws, v) == -5
+
+
+def test_krylov_arguments_rejected_on_host(lib):
+    v = ctypes.c_void_p(0)
+    fake = ctypes.c_void_p(256)
+    ws = lib.gbla_krylov_workspace(16, 8)
+    assert ws > 0 and lib.gbla_krylov_workspace(16, 0) == 0 and lib.gbla_krylov_workspace(-1, 8) == 0
+    st = _lib.KrylovStats()
+    ok = _lib.KrylovOpts(1e-10, 10, 8)
+    for fn in (lib.gbla_gmres_solve, lib.gbla_bicgstab_solve):
+        assert fn(-1, fake, 1, fake, fake, v, 1, v, ctypes.byref(ok), ctypes.byref(st), fake, ws, v) == -1
+        assert fn(4, fake, 3, fake, fake, v, 1, v, ctypes.byref(ok), ctypes.byref(st), fake, ws, v) == -3
+        # factors without pivots (or the reverse)
+        assert fn(4, fake, 4, fake, fake, fake, 4, v, ctypes.byref(ok), ctypes.byref(st), fake, ws, v) == -6
+        bad = _lib.KrylovOpts(-1.0, 10, 8)
+        assert fn(4, fake, 4, fake, fake, v, 1, v, ctypes.byref(bad), ctypes.byref(st), fake, ws, v) == -9
+        bad = _lib.KrylovOpts(1e-10, 10, 129)
+        assert fn(4, fake, 4, fake, fake, v, 1, v, ctypes.byref(bad), ctypes.byref(st), fake, ws, v) == -9
+        assert fn(4, fake, 4, fake, fake, v, 1, v, ctypes.byref(ok), None, fake, ws, v) == -10
+        assert fn(4, fake, 4, fake, fake, v, 1, v, ctypes.byref(ok), ctypes.byref(st), v, ws, v) == 1001
+        # n = 0: converged, nothing touched
+        assert fn(0, v, 1, v, v, v, 1, v, ctypes.byref(ok), ctypes.byref(st), fake, ws, v) == 0
+        assert st.converged == 1

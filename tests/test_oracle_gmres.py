@@ -184,3 +184,61 @@ def test_lowprec_forced_pivot_shortfall_known():
     A = np.array([[0.5, 0.0, 0.0], [-1.0, 1.0, 0.0], [0.75, 0.0, 1.0]])
     assert M.lu_lowprec(A, 3, "fp32", force_ipiv=[3, 2, 3])[3] == 0.25
     assert M.lu_lowprec(A, 3, "fp32", force_ipiv=[2, 3, 3])[3] == 0.0
+
+
+# ------------------------------------------------------------- BiCGSTAB oracle
+def _nonsym(n, seed, shift):
+    rng = np.random.default_rng(seed)
+    return rng.uniform(-1, 1, (n, n)) + shift * np.eye(n)
+
+
+def test_bicgstab_residual_recurrence_is_true_residual():
+    """The updated residual r_i must equal b - A x_i at every step (a dropped or
+    mis-signed term in the x or r update breaks it)."""
+    n = 80
+    A = _nonsym(n, 1, 12.0)
+    b = np.random.default_rng(2).normal(size=n)
+    for k in range(1, 8):
+        x, info = G.bicgstab(A, b, tol=0.0, max_iter=k)
+        true = np.linalg.norm(b - A @ x) / np.linalg.norm(b)
+        assert abs(true - info["relres"][-1]) <= 1e-12
+
+
+def test_bicgstab_multiple_of_identity_one_step():
+    n = 17
+    b = np.arange(1.0, n + 1)
+    x, info = G.bicgstab(3.0 * np.eye(n), b, tol=1e-15, max_iter=10)
+    assert info["iterations"] == 1 and info["converged"] and not info["breakdown"]
+    assert np.abs(x - b / 3.0).max() <= 4 * 2.0 ** -53 * np.abs(b / 3.0).max()
+
+
+def test_bicgstab_exact_preconditioner_one_step():
+    n = 40
+    A = _nonsym(n, 3, 2.0)
+    b = np.random.default_rng(4).normal(size=n)
+    Ainv = np.linalg.inv(A)
+    x, info = G.bicgstab(A, b, tol=1e-12, max_iter=5, apply_minv=lambda v: Ainv @ v)
+    assert info["iterations"] == 1 and info["converged"]
+
+
+def test_bicgstab_converges_to_direct_solution():
+    n = 120
+    A = _nonsym(n, 5, 15.0)
+    b = np.random.default_rng(6).normal(size=n)
+    x, info = G.bicgstab(A, b, tol=1e-13, max_iter=200)
+    assert info["converged"]
+    xd = np.linalg.solve(A, b)
+    assert np.abs(x - xd).max() <= 1e-11 * np.abs(xd).max()
+
+
+def test_bicgstab_matches_scipy_iterates():
+    """SciPy's independent BiCGSTAB, run for the same number of steps from the
+    same start, reaches the same iterate (both FP64; rounding apart)."""
+    sla = pytest.importorskip("scipy.sparse.linalg")
+    n = 60
+    A = _nonsym(n, 7, 10.0)
+    b = np.random.default_rng(8).normal(size=n)
+    for k in (1, 2, 5):
+        x, _ = G.bicgstab(A, b, tol=0.0, max_iter=k)
+        xs, _ = sla.bicgstab(A, b, x0=np.zeros(n), rtol=0.0, atol=0.0, maxiter=k)
+        assert np.abs(x - xs).max() <= 1e-10 * np.abs(xs).max()
