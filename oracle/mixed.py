@@ -178,3 +178,66 @@ def apply_minv_factory(W, ipiv):
         return b
 
     return apply
+
+
+def chol_lowprec(A, nb, prec):
+    """Blocked right-looking Cholesky A = L L^t of fp32(A), lower triangle
+    (paper section 2 for SPD systems), in the mixed precision of lu_lowprec.
+    Per block column k0 .. k1:
+      1. the diagonal block, column by column: d = a_jj, d <= 0 stops with
+         info = j + 1; l_jj = sqrt(d); l_ij = a_ij / l_jj; a_ik -= l_ij l_kj
+         inside the block -- FP64 arithmetic, each stored value rounded to FP32;
+      2. the rows below it, L21 = A21 L11^{-t}, by substitution column by
+         column (FP64 arithmetic, stored FP32);
+      3. the trailing lower triangle A22 -= L21 L21^t with lowprec_product
+         (the same operand rounding and scaling as the LU's update; the row
+         scale of L21 serves both factors).
+    Returns (W with L in its lower triangle, FP32 values in float64; the
+    strict upper triangle is not meaningful), info."""
+    W = to_fp32(np.array(A, dtype=np.float64, order="F"))
+    n = W.shape[0]
+    for k0 in range(0, n, nb):
+        k1 = min(k0 + nb, n)
+        for j in range(k0, k1):
+            d = W[j, j]
+            if not d > 0.0:
+                return W, j + 1
+            W[j, j] = to_fp32(np.sqrt(d))
+            W[j + 1:k1, j] = to_fp32(W[j + 1:k1, j] / W[j, j])
+            if j + 1 < k1:
+                # lower part of the rest of the diagonal block
+                upd = np.tril(np.outer(W[j + 1:k1, j], W[j + 1:k1, j]))
+                W[j + 1:k1, j + 1:k1] = to_fp32(W[j + 1:k1, j + 1:k1] - upd)
+        if k1 >= n:
+            break
+        # 2. L21 = A21 L11^{-t}: column j of L21 = (A21[:, j] - sum_{k<j} L21[:, k] l_jk) / l_jj
+        for j in range(k0, k1):
+            s = W[k1:, j].copy()
+            for k in range(k0, j):
+                s = s - W[k1:, k] * W[j, k]
+            W[k1:, j] = to_fp32(s / W[j, j])
+        # 3. trailing lower triangle
+        L21 = W[k1:, k0:k1]
+        D = lowprec_product(L21, L21.T.copy(), prec)
+        W22 = (W[k1:, k1:].astype(np.float32) - D.astype(np.float32)).astype(np.float64)
+        W[k1:, k1:] = np.tril(W22) + np.triu(W[k1:, k1:], 1)
+    return W, 0
+
+
+def chol_minv_factory(W):
+    """M^{-1} v = L^{-t} L^{-1} v with the FP32-valued factor (lower triangle of
+    W), FP64 arithmetic: forward substitution with L, back substitution with
+    L^t."""
+    n = W.shape[0]
+    Lc = np.tril(W)
+
+    def apply(v):
+        b = np.array(v, dtype=np.float64)
+        for j in range(n):
+            b[j] = b[j] / Lc[j, j]
+            b[j + 1:] -= Lc[j + 1:, j] * b[j]
+        for j in range(n - 1, -1, -1):
+            b[j] = (b[j] - Lc[j + 1:, j] @ b[j + 1:]) / Lc[j, j]
+        return b
+
+    return apply

@@ -242,3 +242,57 @@ def test_bicgstab_matches_scipy_iterates():
         x, _ = G.bicgstab(A, b, tol=0.0, max_iter=k)
         xs, _ = sla.bicgstab(A, b, x0=np.zeros(n), rtol=0.0, atol=0.0, maxiter=k)
         assert np.abs(x - xs).max() <= 1e-10 * np.abs(xs).max()
+
+
+# ------------------------------------------------------ low-precision Cholesky
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16", "fp16", "fp16x3", "bf16x3"])
+@pytest.mark.parametrize("n,nb", [(1, 4), (37, 8), (96, 32)])
+def test_lowprec_chol_dyadic_exact(prec, n, nb):
+    """Integer L (diagonal 1, 2, 4; entries in [-3, 3]): every operand is exact in
+    every update precision and every FP32 sum is exact, so L comes back bit for
+    bit, as does the solution of L L^t x = b for an integer x."""
+    A, L0 = inputs.dyadic_chol(n, seed=900 + n)
+    W, info = M.chol_lowprec(A.numpy(), nb, prec)
+    assert info == 0
+    assert np.array_equal(np.tril(W), L0.numpy())
+    x = np.arange(1.0, n + 1)
+    ap = M.chol_minv_factory(W)
+    assert np.array_equal(ap(A.numpy() @ x), x)
+
+
+@pytest.mark.parametrize("prec,u", [("fp32", 2.0 ** -24), ("bf16", 2.0 ** -8), ("fp16x3", 2.0 ** -21)])
+def test_lowprec_chol_backward_error(prec, u):
+    """||A - L L^t|| <= c n u_p ||L|| ||L^t|| (Cholesky backward stability with the
+    update precision's unit roundoff); the FP32 variant is close to FP64 potrf."""
+    n, nb = 150, 32
+    A = inputs.spd(n, seed=31).numpy()
+    W, info = M.chol_lowprec(A, nb, prec)
+    assert info == 0
+    L = np.tril(W)
+    assert np.abs(A - L @ L.T).max() <= 4 * n * u * (np.abs(L) @ np.abs(L.T)).max()
+    if prec == "fp32":
+        Lo, _ = oracle.potrf(np.asfortranarray(A))
+        assert np.abs(L - np.tril(Lo)).max() <= 8 * n * 2.0 ** -24 * np.abs(np.tril(Lo)).max()
+
+
+def test_lowprec_chol_not_spd():
+    A = inputs.spd(40, seed=32).numpy()
+    A[17, 17] = -1.0
+    _, info = M.chol_lowprec(A, 8, "bf16")
+    assert info == 18
+
+
+def test_chol_gmres_ir_oracle_converges():
+    """SPD system of condition 1e4 (A = U diag(s) U^t, U Haar): GMRES-IR with
+    the fp16x3 Cholesky factors reaches 1e-14 (oracle FP64 matvec)."""
+    n = 200
+    U = inputs.haar(n, 4).numpy()
+    s = 1e4 ** (-np.arange(n) / (n - 1))
+    A = (U * s) @ U.T
+    A = (A + A.T) / 2
+    b = A @ np.random.default_rng(0).normal(size=n)
+    W, info = M.chol_lowprec(A, 32, "fp16x3")
+    assert info == 0
+    x, st = G.gmres_ir(A, b, M.chol_minv_factory(W), tol=1e-14, m=50, max_outer=10)
+    assert st["converged"]
+    assert oracle.backward_error(np.asfortranarray(A), x, b)[0] <= 1e-14
