@@ -492,6 +492,44 @@ def _event_ms(fn, reps=1):
     return e0.elapsed_time(e1) / reps
 
 
+def chol_mixed_vs_fp64(n, args):
+    """Time to backward error <= 1e-14 of the SPD system A x = b: fp16x3 Cholesky +
+    GMRES-IR against the FP64 Cholesky + solve (both tuned, events on the stream)."""
+    from paper_1511_07174_gb300 import api, inputs
+    dev = "cuda"
+    A = inputs.spd_fp32_product(n, 2, dev)
+    b = A @ inputs.normal((n,), 3, dev)
+    F = torch.empty_strided((n, n), (1, n), dtype=torch.float32, device=dev)
+
+    def mixed():
+        Fk, info = api.chol_factor_mixed(A, prec="fp16x3", nb=256, F=F)
+        return api.chol_gmresir(A, Fk, b, tol=1e-14, max_outer=20, restart_m=args.restart)
+
+    mixed()
+    api.prof_enable(["gemm_tc", "trsv", "panel"])
+    api.prof_reset()
+    ms_m = _event_ms(mixed)
+    groups = {k: round(api.prof_read(k)[1], 3) for k in ("gemm_tc", "trsv", "panel")}
+    api.prof_enable([])
+    x, st = mixed()
+    beta_m = float(api.backward_error(A, x, b).item())
+    nbc = api.tune_chol_nb(min(n, 8192))
+
+    def fp64():
+        Lf, info = api.chol_factor(A, nb=nbc)
+        return api.chol_solve(Lf, b)
+
+    ms_d = _event_ms(fp64)
+    beta_d = float(api.backward_error(A, fp64(), b).item())
+    flops = n ** 3 / 3.0
+    return {"n": n, "mixed_ms": ms_m, "mixed_tflops": flops / (ms_m * 1e-3) / 1e12,
+            "mixed_outer": st["outer"], "mixed_inner": st["inner"], "mixed_beta": beta_m,
+            "mixed_kernel_group_ms": groups,
+            "fp64_ms": ms_d, "fp64_tflops": flops / (ms_d * 1e-3) / 1e12, "fp64_beta": beta_d,
+            "fp64_nb": nbc, "speedup_mixed_vs_fp64": ms_d / ms_m,
+            "workload": "A = B B^t/n + I (B iid N(0,1), product in FP32), x_true N(0,1), fp16x3 update"}
+
+
 def secondary(args, pk):
     """The other measured workloads of the solver (one GPU): FP64 LU n = 512 and
     n = 8192 (16 RHS, block size autotuned), FP64 Cholesky n = 8192, the batched
@@ -549,6 +587,9 @@ def secondary(args, pk):
     out["chol_n8192_fp64"] = {"nb": nbc, "factor_ms": ms_c, "tflops": tfc, "frac_of_fp64_dgemm": tfc / fp64_peak,
                               "beta_max": float(api.backward_error(S, Xc, Bs).max().item())}
     del S, F, Xc, A, B
+    # mixed-precision Cholesky + GMRES-IR against the FP64 Cholesky, SPD n = 16384
+    # (A = B B^t / n + I, the product formed in FP32), one right-hand side
+    out["chol_mixed_n16384"] = chol_mixed_vs_fp64(16384, args)
     # batched: 4096 systems n_i in [16, 256], 1-4 RHS, one persistent launch in a CUDA graph
     sizes, nrhs, As, Bs_, Xs_ = inputs.batched(4096, seed=7)
     flops = sum(2.0 / 3.0 * m ** 3 + 2.0 * m * m * k for m, k in zip(sizes, nrhs))

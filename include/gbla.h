@@ -239,6 +239,31 @@ int gbla_gmresir_solve_nrhs(int n, int nrhs, const double *A, int lda, const flo
                             void *d_work, size_t work_bytes, gbla_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Mixed-precision Cholesky + GMRES-IR for symmetric positive definite A
+ * (paper section 2: A = L L^t; the same refinement as for the LU).
+ * gbla_chol_factor_mixed: F (n x n FP32, ldf) <- fp32 of A's lower triangle
+ *   (A is read on and below the diagonal only), factored in place by the
+ *   blocked Cholesky of gbla_chol_factor in FP32 arithmetic with the trailing
+ *   update in `prec` (GBLA_PREC_*; the tensor-core kinds update only the
+ *   tiles on or below the diagonal, from one scaled copy of L21 per outer
+ *   block); nb: outer block width, 64..256, a multiple of 64 (0 = 256). On
+ *   return the lower triangle of F holds L and its strict upper triangle
+ *   holds L^t (for the refinement's back substitution). d_info: 0 or k > 0
+ *   when the leading minor of order k is not positive (in FP32 arithmetic).
+ * gbla_chol_gmresir_solve_nrhs: gbla_gmresir_solve_nrhs with M = L L^t from
+ *   those factors (no pivots). A must hold the whole symmetric matrix (the
+ *   FP64 residual reads both triangles). Workspace: gbla_gmresir_workspace.
+ * ------------------------------------------------------------------------ */
+size_t gbla_chol_factor_mixed_workspace(int n, int nb, int prec);
+int gbla_chol_factor_mixed(int n, const double *A, int lda, float *F, int ldf, int *d_info,
+                           int prec, int nb, void *d_work, size_t work_bytes,
+                           gbla_stream_t stream);
+int gbla_chol_gmresir_solve_nrhs(int n, int nrhs, const double *A, int lda, const float *F,
+                                 int ldf, const double *B, int ldb, double *X, int ldx,
+                                 const gbla_gmresir_opts *opts, gbla_gmresir_stats *stats,
+                                 void *d_work, size_t work_bytes, gbla_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Standalone Krylov solvers (paper section 2: the non-stationary iterative
  * methods -- GMRES with Gram-Schmidt orthogonalisation and restarts, and
  * BiCGSTAB -- next to the direct solvers), FP64 on a dense A (n x n, lda),

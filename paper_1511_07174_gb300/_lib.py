@@ -68,6 +68,11 @@ _SIGS = {
     "gbla_gmresir_solve_nrhs": ([_i, _i, _vp, _i, _vp, _i, _vp, _vp, _i, _vp, _i,
                                  ctypes.POINTER(GmresirOpts), ctypes.POINTER(GmresirStats), _vp, _sz,
                                  _vp], _i),
+    "gbla_chol_factor_mixed_workspace": ([_i, _i, _i], _sz),
+    "gbla_chol_factor_mixed": ([_i, _vp, _i, _vp, _i, _vp, _i, _i, _vp, _sz, _vp], _i),
+    "gbla_chol_gmresir_solve_nrhs": ([_i, _i, _vp, _i, _vp, _i, _vp, _i, _vp, _i,
+                                      ctypes.POINTER(GmresirOpts), ctypes.POINTER(GmresirStats), _vp,
+                                      _sz, _vp], _i),
     "gbla_krylov_workspace": ([_i, _i], _sz),
     "gbla_gmres_solve": ([_i, _vp, _i, _vp, _vp, _vp, _i, _vp, ctypes.POINTER(KrylovOpts),
                           ctypes.POINTER(KrylovStats), _vp, _sz, _vp], _i),

@@ -236,6 +236,57 @@ def bicgstab(A, b, x0=None, tol=1e-10, max_iter=1000, F=None, ipiv=None):
     return _krylov("gbla_bicgstab_solve", A, b, x0, tol, max_iter, 1, F, ipiv)
 
 
+def chol_factor_mixed(A, prec="fp16x3", nb=256, F=None):
+    """Low-precision Cholesky of fp32(A) (A SPD; its lower triangle is read).
+    Returns (F FP32: L in the lower triangle, L^t in the strict upper one, info)."""
+    _require_cuda(A)
+    L = _lib.load()
+    n = A.shape[0]
+    Ac = colmajor(A, torch.float64)
+    if F is None:
+        F = torch.empty_strided((n, n), (1, max(1, n)), dtype=torch.float32, device=A.device)
+    info = torch.zeros(1, dtype=torch.int32, device=A.device)
+    p = PREC[prec] if isinstance(prec, str) else int(prec)
+    ws = _ws(L.gbla_chol_factor_mixed_workspace(n, nb, p), A.device)
+    _check("gbla_chol_factor_mixed",
+           L.gbla_chol_factor_mixed(n, _p(Ac), _ld(Ac), _p(F), _ld(F), _p(info), p, nb, _p(ws),
+                                    ws.numel(), _stream()))
+    return F, info
+
+
+def chol_gmresir(A, F, b, tol=1e-14, inner_tol=1e-8, max_outer=10, restart_m=50, restarts=1):
+    """GMRES-based refinement with the mixed Cholesky factors (A: the whole SPD
+    matrix, FP64). b: a vector or an n x k matrix. Returns (x or X, stats dict or list)."""
+    _require_cuda(A, F, b)
+    L = _lib.load()
+    n = A.shape[0]
+    Ac = colmajor(A, torch.float64)
+    Fc = colmajor(F, torch.float32)
+    vec = b.dim() == 1
+    Bc = colmajor(b, torch.float64)
+    k = Bc.shape[1]
+    X = torch.empty_strided((n, k), (1, max(1, n)), dtype=torch.float64, device=A.device)
+    opts = _lib.GmresirOpts(tol, inner_tol, max_outer, restart_m, restarts)
+    st = (_lib.GmresirStats * max(k, 1))()
+    ws = _ws(L.gbla_gmresir_workspace(n, restart_m), A.device)
+    rc = L.gbla_chol_gmresir_solve_nrhs(n, k, _p(Ac), _ld(Ac), _p(Fc), _ld(Fc), _p(Bc), _ld(Bc), _p(X),
+                                        _ld(X), ctypes.byref(opts), st, _p(ws), ws.numel(), _stream())
+    if rc not in (0, _lib.GBLA_ERR_NOT_CONVERGED):
+        raise GblaError("gbla_chol_gmresir_solve_nrhs", rc)
+    sts = [_stats_dict(st[j]) for j in range(k)]
+    return (X[:, 0], sts[0]) if vec else (X, sts)
+
+
+def solve_chol_mixed(A, b, prec="fp16x3", nb=256, **kw):
+    """Mixed-precision Cholesky + GMRES-IR for SPD A. Returns (x, stats)."""
+    F, info = chol_factor_mixed(A, prec, nb)
+    x, st = chol_gmresir(A, F, b, **kw)
+    inf = int(info.item())
+    for d in (st if isinstance(st, list) else [st]):
+        d["info"] = inf
+    return x, st
+
+
 def backward_error(A, X, B):
     """Per-column ||B - A X||_inf / (||A||_inf ||X||_inf) on the device (FP64)."""
     _require_cuda(A, X, B)

@@ -235,11 +235,11 @@ cudaError_t blocked_lu(int n, Ts* A, int lda, int* ipiv, int* info, int nb, int 
     if (tensor) {
       if constexpr (sizeof(Ts) == 4) {
         PROF(KK_CONVERT, s, launch_convert_rows(reinterpret_cast<const float*>(A + (k0 + kb) + (size_t)k0 * lda), lda,
-                                nt, kb, prec, w.Ak, w.ldk, w.eA, s));
+                                nt, kb, prec, w.Ak, w.ldk, w.eA, false, s));
         if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
         PROF(KK_GEMM_TC, s, launch_gemm_tc(prec_mma_kind(prec), nt, nt, prec_kmult(prec) * kb, w.Ak, w.ldk, w.Bk, w.ldk, w.eA, w.eB,
                            reinterpret_cast<float*>(A + (k0 + kb) + (size_t)(k0 + kb) * lda), lda,
-                           info, s));
+                           info, false, s));
         if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
       } else {
         return cudaErrorInvalidValue;
@@ -888,29 +888,29 @@ static int gmresir_one(int n, const double* A, int lda, const float* F, int ldf,
 }
 
 // Per-call set-up of the refinement: the permutation of the pivots, the
-// inverted diagonal blocks of L and U, ||A||_inf.
+// inverted diagonal blocks of L and U, ||A||_inf. Cholesky factors (ipiv
+// null): no interchanges, L with its own diagonal, L^t in the upper triangle.
 static int gmresir_setup(int n, const double* A, int lda, const float* F, int ldf, const int* ipiv,
                          const IrWork& w, cudaStream_t s) {
   GBLA_TRY(cudaMemsetAsync(w.info, 0, sizeof(int), s));
   GBLA_TRYK(KK_PERM, s, launch_ipiv_to_perm(n, ipiv, w.perm, s));
-  GBLA_TRYK(KK_TRSV, s, launch_diag_inv<float>(true, true, n, F, ldf, w.DinvL, s));
+  GBLA_TRYK(KK_TRSV, s, launch_diag_inv<float>(true, ipiv != nullptr, n, F, ldf, w.DinvL, s));
   GBLA_TRYK(KK_TRSV, s, launch_diag_inv<float>(false, false, n, F, ldf, w.DinvU, s));
   GBLA_TRYK(KK_MATVEC, s, launch_row_abs_sum_max(n, A, lda, w.part, w.anorm, s));
   return GBLA_OK;
 }
 
-int gbla_gmresir_solve_nrhs(int n, int nrhs, const double* A, int lda, const float* F, int ldf,
-                            const int* ipiv, const double* B, int ldb, double* X, int ldx,
-                            const gbla_gmresir_opts* opts, gbla_gmresir_stats* stats,
-                            void* d_work, size_t work_bytes, gbla_stream_t stream) {
-  clear_error();
+static int gmresir_nrhs(int n, int nrhs, const double* A, int lda, const float* F, int ldf,
+                        const int* ipiv, const double* B, int ldb, double* X, int ldx,
+                        const gbla_gmresir_opts* opts, gbla_gmresir_stats* stats, void* d_work,
+                        size_t work_bytes, gbla_stream_t stream, bool chol) {
   if (n < 0) return -1;
   if (nrhs < 0) return -2;
   if (n > 0 && !A) return -3;
   if (lda < std::max(1, n)) return -4;
   if (n > 0 && !F) return -5;
   if (ldf < std::max(1, n)) return -6;
-  if (n > 0 && !ipiv) return -7;
+  if (!chol && n > 0 && !ipiv) return -7;
   if (n > 0 && nrhs > 0 && !B) return -8;
   if (ldb < std::max(1, n)) return -9;
   if (n > 0 && nrhs > 0 && !X) return -10;
@@ -931,7 +931,7 @@ int gbla_gmresir_solve_nrhs(int n, int nrhs, const double* A, int lda, const flo
   if (nrhs == 0) return GBLA_OK;
   const DeviceProps& dp = device_props();
   if (!dp.coop) return GBLA_ERR_DEVICE;
-  int rc = gmresir_setup(n, A, lda, F, ldf, ipiv, w, s);
+  int rc = gmresir_setup(n, A, lda, F, ldf, chol ? nullptr : ipiv, w, s);
   if (rc != GBLA_OK) return rc;
   int all = GBLA_OK;
   for (int k = 0; k < nrhs; ++k) {
@@ -940,6 +940,86 @@ int gbla_gmresir_solve_nrhs(int n, int nrhs, const double* A, int lda, const flo
     else if (rc != GBLA_OK) return rc;
   }
   return all;
+}
+
+int gbla_gmresir_solve_nrhs(int n, int nrhs, const double* A, int lda, const float* F, int ldf,
+                            const int* ipiv, const double* B, int ldb, double* X, int ldx,
+                            const gbla_gmresir_opts* opts, gbla_gmresir_stats* stats,
+                            void* d_work, size_t work_bytes, gbla_stream_t stream) {
+  clear_error();
+  return gmresir_nrhs(n, nrhs, A, lda, F, ldf, ipiv, B, ldb, X, ldx, opts, stats, d_work, work_bytes,
+                      stream, false);
+}
+
+int gbla_chol_gmresir_solve_nrhs(int n, int nrhs, const double* A, int lda, const float* F, int ldf,
+                                 const double* B, int ldb, double* X, int ldx,
+                                 const gbla_gmresir_opts* opts, gbla_gmresir_stats* stats,
+                                 void* d_work, size_t work_bytes, gbla_stream_t stream) {
+  clear_error();
+  const int rc = gmresir_nrhs(n, nrhs, A, lda, F, ldf, nullptr, B, ldb, X, ldx, opts, stats, d_work,
+                              work_bytes, stream, true);
+  // argument positions of this entry point (no ipiv)
+  return rc < 0 && rc <= -8 ? rc + 1 : rc;
+}
+
+// ---------------------------------------------------------------------------
+// Mixed-precision Cholesky (steps a1, a3, a4 for SPD systems in low
+// precision): F <- fp32 of A's lower triangle, factored in place; the strict
+// upper triangle of F receives L^t for the refinement's back substitution.
+static size_t chol_mixed_layout(Carver& c, int n, int nb, int prec, void** Ak, void** Bk, int** eA,
+                                int* ldk) {
+  const int elem = prec == GBLA_PREC_TF32 ? 4 : 2;
+  const int lk = ((prec_kmult(prec) * nb + 63) / 64) * 64;
+  void* a = nullptr;
+  void* b = nullptr;
+  int* e = nullptr;
+  if (prec_is_tensor(prec)) {
+    a = c.take<char>((size_t)std::max(n, 1) * lk * elem);
+    if (prec_is_split(prec)) b = c.take<char>((size_t)std::max(n, 1) * lk * elem);
+    e = c.take<int>((size_t)std::max(n, 1));
+  } else {
+    c.take<int>(1);
+  }
+  if (Ak) *Ak = a;
+  if (Bk) *Bk = b;
+  if (eA) *eA = e;
+  if (ldk) *ldk = lk;
+  return c.off;
+}
+
+size_t gbla_chol_factor_mixed_workspace(int n, int nb, int prec) {
+  if (nb == 0) nb = 256;
+  if (n < 0 || nb % 64 != 0 || nb < 64 || nb > 256 || prec < GBLA_PREC_FP32 || prec > GBLA_PREC_BF16X3)
+    return 0;
+  Carver c(nullptr, 0);
+  return chol_mixed_layout(c, n, nb, prec, nullptr, nullptr, nullptr, nullptr);
+}
+
+int gbla_chol_factor_mixed(int n, const double* A, int lda, float* F, int ldf, int* d_info, int prec,
+                           int nb, void* d_work, size_t work_bytes, gbla_stream_t stream) {
+  clear_error();
+  if (n < 0) return -1;
+  if (n > 0 && !A) return -2;
+  if (lda < std::max(1, n)) return -3;
+  if (n > 0 && !F) return -4;
+  if (ldf < std::max(1, n)) return -5;
+  if (!d_info) return -6;
+  if (prec < GBLA_PREC_FP32 || prec > GBLA_PREC_BF16X3) return -7;
+  if (nb == 0) nb = 256;
+  if (nb % 64 != 0 || nb < 64 || nb > 256) return -8;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!d_work || !aligned256(d_work)) return GBLA_ERR_WORKSPACE;
+  Carver c(d_work, work_bytes);
+  void* Ak = nullptr;
+  void* Bk = nullptr;
+  int* eA = nullptr;
+  int ldk = 0;
+  chol_mixed_layout(c, n, nb, prec, &Ak, &Bk, &eA, &ldk);
+  if (!c.ok) return GBLA_ERR_WORKSPACE;
+  GBLA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), s));
+  if (n == 0) return GBLA_OK;
+  GBLA_TRYK(KK_COPY, s, launch_copy_d2f(A, lda, F, ldf, n, n, s, true));
+  return cuda_status(launch_chol_mixed(n, F, ldf, nb, prec, Ak, Bk, ldk, eA, d_info, s));
 }
 
 int gbla_gmresir_solve(int n, const double* A, int lda, const float* F, int ldf, const int* ipiv,

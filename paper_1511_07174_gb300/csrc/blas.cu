@@ -461,7 +461,9 @@ template cudaError_t launch_gemm_simt<float>(int, int, int, float, const float*,
 // ----------------------------------------------------------------------------
 // L21 (FP32, M x K column-major) -> K-major low-precision rows with one
 // power-of-two exponent per row. CTA: 32 rows; shared-memory transpose.
-template <int KIND>
+// LEFT: the left operand's pattern for the split kinds ([hi | hi | lo]);
+// otherwise the right operand's ([hi | lo | hi]).
+template <int KIND, bool LEFT>
 __global__ void __launch_bounds__(256)
     convert_rows_kernel(const float* __restrict__ F, int ldf, int M, int K, void* __restrict__ outK,
                         int ldk, int* __restrict__ outE) {
@@ -499,7 +501,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int t = 0; t < 2; ++t) {
           const int kk = lane * 2 + t, k = k0 + kk;
-          if (k < K) store_lowp<KIND, true>(outK, (size_t)mr * ldk, K, k, ldexpf(tile[kk][mm], es[mm]));
+          if (k < K) store_lowp<KIND, LEFT>(outK, (size_t)mr * ldk, K, k, ldexpf(tile[kk][mm], es[mm]));
         }
       }
     }
@@ -508,49 +510,47 @@ __global__ void __launch_bounds__(256)
 }
 
 cudaError_t launch_convert_rows(const float* F, int ldf, int M, int K, int kind, void* outK,
-                                int ldk, int* outE, cudaStream_t s) {
+                                int ldk, int* outE, bool right, cudaStream_t s) {
   if (M <= 0 || K <= 0) return cudaSuccess;
   dim3 grid((M + 31) / 32);
+#define GBLA_CONV(KD)                                                                          \
+  if (right)                                                                                   \
+    convert_rows_kernel<KD, false><<<grid, 256, 0, s>>>(F, ldf, M, K, outK, ldk, outE);        \
+  else                                                                                         \
+    convert_rows_kernel<KD, true><<<grid, 256, 0, s>>>(F, ldf, M, K, outK, ldk, outE);
   switch (kind) {
-    case GBLA_PREC_BF16:
-      convert_rows_kernel<GBLA_PREC_BF16><<<grid, 256, 0, s>>>(F, ldf, M, K, outK, ldk, outE);
-      break;
-    case GBLA_PREC_FP16:
-      convert_rows_kernel<GBLA_PREC_FP16><<<grid, 256, 0, s>>>(F, ldf, M, K, outK, ldk, outE);
-      break;
-    case GBLA_PREC_TF32:
-      convert_rows_kernel<GBLA_PREC_TF32><<<grid, 256, 0, s>>>(F, ldf, M, K, outK, ldk, outE);
-      break;
-    case GBLA_PREC_FP16X3:
-      convert_rows_kernel<GBLA_PREC_FP16X3><<<grid, 256, 0, s>>>(F, ldf, M, K, outK, ldk, outE);
-      break;
-    case GBLA_PREC_BF16X3:
-      convert_rows_kernel<GBLA_PREC_BF16X3><<<grid, 256, 0, s>>>(F, ldf, M, K, outK, ldk, outE);
-      break;
+    case GBLA_PREC_BF16: GBLA_CONV(GBLA_PREC_BF16) break;
+    case GBLA_PREC_FP16: GBLA_CONV(GBLA_PREC_FP16) break;
+    case GBLA_PREC_TF32: GBLA_CONV(GBLA_PREC_TF32) break;
+    case GBLA_PREC_FP16X3: GBLA_CONV(GBLA_PREC_FP16X3) break;
+    case GBLA_PREC_BF16X3: GBLA_CONV(GBLA_PREC_BF16X3) break;
     default:
       return cudaErrorInvalidValue;
   }
+#undef GBLA_CONV
   count_launch();
   return cudaGetLastError();
 }
 
 // ----------------------------------------------------------------------------
+// lower: rows r >= column only (the strict upper triangle of F is left as is)
 __global__ void copy_d2f_kernel(const double* __restrict__ A, int lda, float* __restrict__ F,
-                                int ldf, int m, int n) {
+                                int ldf, int m, int c0, int lower) {
   const int col = blockIdx.y;
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x)
+  const int r0 = lower ? c0 + col : 0;
+  for (int r = r0 + blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x)
     F[r + (size_t)col * ldf] = (float)A[r + (size_t)col * lda];
 }
 
 cudaError_t launch_copy_d2f(const double* A, int lda, float* F, int ldf, int m, int n,
-                            cudaStream_t s) {
+                            cudaStream_t s, bool lower) {
   if (m <= 0 || n <= 0) return cudaSuccess;
   int bx = (m + 255) / 256;
   if (bx > 16) bx = 16;
   for (int c0 = 0; c0 < n; c0 += 65535) {
     const int nc = n - c0 < 65535 ? n - c0 : 65535;
     copy_d2f_kernel<<<dim3(bx, nc), 256, 0, s>>>(A + (size_t)c0 * lda, lda, F + (size_t)c0 * ldf,
-                                                 ldf, m, nc);
+                                                 ldf, m, c0, lower ? 1 : 0);
     count_launch();
   }
   return cudaGetLastError();
@@ -586,8 +586,17 @@ __global__ void ipiv_to_perm_kernel(int n, const int* __restrict__ ipiv, int* __
     for (int i = threadIdx.x; i < n; i += blockDim.x) perm[i] = p[i];
 }
 
+__global__ void iota_kernel(int n, int* __restrict__ perm) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) perm[i] = i;
+}
+
 cudaError_t launch_ipiv_to_perm(int n, const int* ipiv, int* perm, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
+  if (!ipiv) {  // no interchanges: the identity
+    iota_kernel<<<(n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024, 256, 0, s>>>(n, perm);
+    count_launch();
+    return cudaGetLastError();
+  }
   const DeviceProps& dp = device_props();
   const size_t bytes = (size_t)2 * n * sizeof(int);
   const int use_smem = bytes + 1024 <= dp.smem_optin ? 1 : 0;

@@ -129,6 +129,21 @@ GBLA_DEVINL void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Output tile t -> (row tile, column tile): column-major over the tile grid,
+// or, for the lower triangle of tiles, row by row over (i, j), j <= i.
+GBLA_DEVINL void tile_coords(int t, int tilesM, int lower, int& ti, int& tj) {
+  if (!lower) {
+    ti = t % tilesM;
+    tj = t / tilesM;
+    return;
+  }
+  int i = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+  while ((long long)(i + 1) * (i + 2) / 2 <= t) ++i;
+  while ((long long)i * (i + 1) / 2 > t) --i;
+  ti = i;
+  tj = t - i * (i + 1) / 2;
+}
+
 // 2^e for |e| <= 126, built from the exponent field (exact).
 GBLA_DEVINL float pow2f(int e) { return __int_as_float((127 + e) << 23); }
 
@@ -176,6 +191,7 @@ GBLA_DEVINL void mbar_arrive(uint32_t bar) {
 
 struct PsArgs {
   int M, N, K, tilesM, ntiles;
+  int lower;  // enumerate only the tiles (i, j) with i >= j (M == N)
   float* C;
   int ldc;
   const int* eA;
@@ -245,7 +261,9 @@ __global__ void __launch_bounds__(kPsThreads, 1)
       int it = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < args.ntiles && ok; t += gridDim.x) {
-        const int m0 = (t % args.tilesM) * kTcBM, n0 = (t / args.tilesM) * kTcBN;
+        int ti, tj;
+        tile_coords(t, args.tilesM, args.lower, ti, tj);
+        const int m0 = ti * kTcBM, n0 = tj * kTcBN;
         for (int kb = 0; kb < KB; ++kb, ++it) {
           const int st = it % kPsStages;
           const uint32_t ph = (uint32_t)((it / kPsStages) & 1);
@@ -314,7 +332,9 @@ __global__ void __launch_bounds__(kPsThreads, 1)
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int m0 = (t % args.tilesM) * kTcBM, n0 = (t / args.tilesM) * kTcBN;
+      int ti, tj;
+      tile_coords(t, args.tilesM, args.lower, ti, tj);
+      const int m0 = ti * kTcBM, n0 = tj * kTcBN;
       const int row = m0 + eg * 32 + lane;
       const bool rok = row < args.M;
       const float sa = (rok && args.eA) ? pow2f(-args.eA[row]) : 1.0f;
@@ -434,8 +454,9 @@ static bool encode_kmajor(CUtensorMap* map, int kind, const void* ptr, int K, in
 
 cudaError_t launch_gemm_tc(int kind, int M, int N, int K, const void* Ak, int ldak, const void* Bk,
                            int ldbk, const int* eA, const int* eB, float* C, int ldc, int* info,
-                           cudaStream_t s) {
+                           bool lower, cudaStream_t s) {
   if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+  if (lower && M != N) return cudaErrorInvalidValue;
   const int elem = kind == GBLA_PREC_TF32 ? 4 : 2;
   if (((size_t)ldak * elem) % 16 != 0 || ((size_t)ldbk * elem) % 16 != 0) return cudaErrorInvalidValue;
   if ((reinterpret_cast<uintptr_t>(Ak) & 15) || (reinterpret_cast<uintptr_t>(Bk) & 15))
@@ -444,7 +465,8 @@ cudaError_t launch_gemm_tc(int kind, int M, int N, int K, const void* Ak, int ld
   if (!encode_kmajor(&ta, kind, Ak, K, M, ldak)) return cudaErrorInvalidValue;
   if (!encode_kmajor(&tb, kind, Bk, K, N, ldbk)) return cudaErrorInvalidValue;
   const int tilesM = (M + kTcBM - 1) / kTcBM, tilesN = (N + kTcBN - 1) / kTcBN;
-  PsArgs a{M, N, K, tilesM, tilesM * tilesN, C, ldc, eA, eB, info, wait_timeout_ns()};
+  const int ntiles = lower ? tilesM * (tilesM + 1) / 2 : tilesM * tilesN;
+  PsArgs a{M, N, K, tilesM, ntiles, lower ? 1 : 0, C, ldc, eA, eB, info, wait_timeout_ns()};
   const DeviceProps& dp = device_props();
   int grid = dp.num_sms > 0 ? dp.num_sms : 1;
   if (grid > a.ntiles) grid = a.ntiles;

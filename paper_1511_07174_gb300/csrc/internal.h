@@ -157,17 +157,21 @@ cudaError_t launch_gemm_simt(int M, int N, int K, T alpha, const T* A, int lda, 
                              cudaStream_t s);
 
 // K-major low-precision copy of an FP32 M x K block (rows scaled per row).
+// right: the split kinds' right-operand pattern [hi | lo | hi] (else [hi | hi | lo]).
 cudaError_t launch_convert_rows(const float* F, int ldf, int M, int K, int kind, void* outK,
-                                int ldk, int* outE, cudaStream_t s);
+                                int ldk, int* outE, bool right, cudaStream_t s);
 
+// F = fp32(A) (m x n); lower: only the elements on or below the diagonal.
 cudaError_t launch_copy_d2f(const double* A, int lda, float* F, int ldf, int m, int n,
-                            cudaStream_t s);
+                            cudaStream_t s, bool lower = false);
 
 // tcgen05 trailing update: C (M x N FP32) -= 2^-eA[i] * (A_k B_k^t)[i,j] * 2^-eB[j].
 // A_k: M rows of K elements (row stride ldak elements), B_k: N rows of K (ldbk).
+// lower (M == N): only the 128 x 128 tiles on or below the diagonal (the
+// diagonal tiles are updated whole, upper part included).
 cudaError_t launch_gemm_tc(int kind, int M, int N, int K, const void* Ak, int ldak,
                            const void* Bk, int ldbk, const int* eA, const int* eB, float* C,
-                           int ldc, int* info, cudaStream_t s);
+                           int ldc, int* info, bool lower, cudaStream_t s);
 
 // ---- triangular solves ------------------------------------------------------
 // uplo_lower: the stored triangle; trans: solve with its transpose; unit: unit diagonal.
@@ -189,6 +193,7 @@ cudaError_t launch_trsv_inv(bool lower, int n, const Ts* T, int ldt, const doubl
                             const double* rhs, double* X, unsigned* flags, int* info,
                             cudaStream_t s);
 
+// ipiv == nullptr: the identity
 cudaError_t launch_ipiv_to_perm(int n, const int* ipiv, int* perm, cudaStream_t s);
 // dst[i, c] = src[perm[i], c] (forward) or dst[perm[i], c] = src[i, c] (inverse)
 cudaError_t launch_permute_rows(int n, int nrhs, const int* perm, bool inverse, const double* src,
@@ -262,6 +267,12 @@ cudaError_t launch_chol_batched(int batch, const int* n, T* const* A, const int*
 // ---- Cholesky (chol.cu) ------------------------------------------------------
 // nb: outer block width, a multiple of 64 up to 256 (0: 64)
 cudaError_t launch_chol(int n, double* A, int lda, int nb, int* info, cudaStream_t s);
+// Mixed-precision Cholesky of the FP32 lower triangle of F (see chol.cu); the
+// strict upper triangle receives L^t. Ak, Bk: K-major copies (n x ldk of the
+// precision's element), eA: n ints.
+cudaError_t launch_chol_mixed(int n, float* F, int ldf, int nb, int prec, void* Ak, void* Bk, int ldk,
+                              int* eA, int* info, cudaStream_t s);
+cudaError_t launch_mirror_lower(int n, float* F, int ldf, cudaStream_t s);
 
 // ---- blocked LU driver (api.cu) ---------------------------------------------
 struct LuWork {

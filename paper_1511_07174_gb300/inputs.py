@@ -13,6 +13,8 @@ measured on):
   spd            A = B B^t / n + I, B iid N(0, 1)
   haar_kappa     A = U diag(s) V^t, U, V Haar orthogonal (QR of Gaussian,
                  sign-fixed), s_i = kappa^(-i/(n-1)) geometric from 1 to 1/kappa
+  haar_spd       A = U diag(s) U^t, the SPD counterpart (same U and s)
+  spd_fp32_product  B B^t / n + I with the product formed in FP32 (large n)
   batched        4096 systems, n_i iid uniform integers in [16, 256],
                  A_i iid U[-1, 1] + n_i I, nrhs_i uniform in {1..4}
   autograd       A iid U[-1, 1] + sqrt(n) I, x_true N(0, 1), g N(0, 1)
@@ -74,6 +76,27 @@ def haar_kappa(n, kappa, seed_u=4, seed_v=5, device="cpu", UV=None):
     U, V = UV if UV is not None else (haar(n, seed_u, device), haar(n, seed_v, device))
     s = kappa_spectrum(n, kappa, device)
     return (U * s.unsqueeze(0)) @ V.t()
+
+
+def haar_spd(n, kappa, seed_u=4, device="cpu", U=None):
+    """Symmetric positive definite A = U diag(s) U^t (U Haar, s geometric from 1
+    to 1/kappa), symmetrised exactly: 2-norm condition number kappa."""
+    U = haar(n, seed_u, device) if U is None else U
+    s = kappa_spectrum(n, kappa, device)
+    A = (U * s.unsqueeze(0)) @ U.t()
+    return (A + A.t()) * 0.5
+
+
+def spd_fp32_product(n, seed, device="cpu"):
+    """A = B B^t / n + I with B iid N(0, 1), the product formed in FP32 (fast at
+    large n) and symmetrised in FP64; SPD with eigenvalues in about [1, 5]."""
+    g = _gen(seed, device)
+    B = torch.randn((n, n), generator=g, dtype=torch.float32, device=device)
+    P = (B @ B.t()).to(torch.float64) / n
+    del B
+    P = (P + P.t()) * 0.5
+    P.diagonal().add_(1.0)
+    return P
 
 
 def rhs_from_solution(A, x_true):
