@@ -81,12 +81,16 @@ const char *gbla_last_error(void);
  *   6 trsv, 7 matvec, 8 mgs, 9 gmres_update, 10 permute, 11 copy, 12 batched.
  * gbla_prof_read: number of recorded groups of `kind` and their summed
  *   device time in ms (waits for the events). gbla_prof_reset forgets them.
+ * gbla_prof_list: the same groups one by one.
  */
 uint64_t gbla_launch_count(void);
 const char *gbla_kernel_kind_name(int kind);
 void gbla_prof_enable(unsigned mask);
 void gbla_prof_reset(void);
 int gbla_prof_read(int kind, int *count, double *total_ms);
+/* Device times (ms) of the first max_count recorded groups of `kind`, in
+ * launch order; returns how many were written (or < 0 for a bad argument). */
+int gbla_prof_list(int kind, int max_count, double *ms);
 
 /*
  * Limit, in nanoseconds, for every inter-CTA wait of later calls (panel

@@ -393,6 +393,15 @@ def prof_read(kind):
     return c.value, t.value
 
 
+def prof_list(kind, max_count=100000):
+    """Device ms of each recorded group of one kind, in launch order."""
+    buf = (ctypes.c_double * max_count)()
+    c = _lib.load().gbla_prof_list(KERNEL_KINDS.index(kind), max_count, buf)
+    if c < 0:
+        raise GblaError("gbla_prof_list", c)
+    return [buf[i] for i in range(c)]
+
+
 # ------------------------------------------------------------------ autotuning
 def _tune_nb(kind, n, candidates, run, device, use_cache):
     from . import batched as _b

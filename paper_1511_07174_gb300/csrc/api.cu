@@ -333,6 +333,23 @@ int gbla_prof_read(int kind, int* count, double* total_ms) {
   return GBLA_OK;
 }
 
+int gbla_prof_list(int kind, int max_count, double* ms) {
+  if (kind < 0 || kind >= KK_COUNT) return -1;
+  if (max_count < 0) return -2;
+  if (max_count > 0 && !ms) return -3;
+  std::lock_guard<std::mutex> lock(g_prof_mu);
+  int c = 0;
+  for (auto& r : g_prof_recs) {
+    if (r.kind != kind) continue;
+    if (c >= max_count) break;
+    if (cudaEventSynchronize(r.b) != cudaSuccess) return GBLA_ERR_CUDA;
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) return GBLA_ERR_CUDA;
+    ms[c++] = t;
+  }
+  return c;
+}
+
 void gbla_set_wait_timeout_ns(uint64_t ns) { g_wait_ns = ns; }
 uint64_t gbla_get_wait_timeout_ns(void) { return g_wait_ns; }
 

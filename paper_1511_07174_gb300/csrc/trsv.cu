@@ -201,7 +201,9 @@ namespace gbla {
 
 // Dinv + b*64*64: column-major inverse of diagonal block b (zero-padded when
 // the last block has fewer than 64 rows). One 64-thread CTA per block; thread
-// j forms column j by substitution against e_j.
+// j forms column j by substitution against e_j. The same array then holds
+// W (at nblk * 64 * 64) and V (at 2 nblk * 64 * 64) per block, and the
+// substitution's partial-sum slots (see trsv_inv_kernel).
 template <typename Ts, bool LOWER, bool UNIT>
 __global__ void __launch_bounds__(64)
     diag_inv_kernel(int n, const Ts* __restrict__ T, int ldt, double* __restrict__ Dinv) {
@@ -245,6 +247,12 @@ __global__ void __launch_bounds__(64)
   for (int i = 0; i < kTsBS; ++i) out[i] = x[i];
 }
 
+template <typename Ts, bool FWD>
+__global__ void __launch_bounds__(256)
+    trsv_wv_kernel(int n, const Ts* __restrict__ T, int ldt, double* __restrict__ Dinv);
+// shared memory of trsv_wv_kernel: D_s (64 x 64) and one tile (64 x 65), FP64
+constexpr size_t kWvSmemBytes = sizeof(double) * ((size_t)kTsBS * kTsBS + (size_t)kTsBS * (kTsBS + 1));
+
 template <typename Ts>
 cudaError_t launch_diag_inv(bool lower, bool unit, int n, const Ts* T, int ldt, double* Dinv,
                             cudaStream_t s) {
@@ -255,22 +263,115 @@ cudaError_t launch_diag_inv(bool lower, bool unit, int n, const Ts* T, int ldt, 
   else if (unit) diag_inv_kernel<Ts, false, true><<<nblk, 64, 0, s>>>(n, T, ldt, Dinv);
   else diag_inv_kernel<Ts, false, false><<<nblk, 64, 0, s>>>(n, T, ldt, Dinv);
   count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || nblk < 2) return e;
+  // W_s = D_s T(s, s-1), V_s = D_s T(s, s-2) in solve order
+  if (lower) {
+    e = ensure_dyn_smem(trsv_wv_kernel<Ts, true>, kWvSmemBytes);
+    if (e != cudaSuccess) return e;
+    trsv_wv_kernel<Ts, true><<<dim3(nblk, 2), 256, kWvSmemBytes, s>>>(n, T, ldt, Dinv);
+  } else {
+    e = ensure_dyn_smem(trsv_wv_kernel<Ts, false>, kWvSmemBytes);
+    if (e != cudaSuccess) return e;
+    trsv_wv_kernel<Ts, false><<<dim3(nblk, 2), 256, kWvSmemBytes, s>>>(n, T, ldt, Dinv);
+  }
+  count_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_diag_inv<float>(bool, bool, int, const float*, int, double*, cudaStream_t);
 template cudaError_t launch_diag_inv<double>(bool, bool, int, const double*, int, double*, cudaStream_t);
 
-size_t diag_inv_doubles(int n) { return (size_t)((n + kTsBS - 1) / kTsBS) * kTsBS * kTsBS; }
 
-// One right-hand side, forward (lower factor) or backward (upper factor).
-// The solution goes to X, which the launcher first fills with an all-ones bit
-// pattern (a NaN that arithmetic does not produce): a block's x values
-// announce themselves, so a consumer polls the 64 values it needs instead of a
-// flag followed by a second load, and the producer needs no fence.
-// Thread (r, g) = (tid % 64, tid / 64) keeps, in registers, elements
-// (r, g + 4i), i < 16, of each 64 x 64 tile of its row block; the tile of the
-// next earlier block is loaded while the current one waits for its x.
+// ---------------------------------------------------------------------------
+// One right-hand side, forward (lower factor) or backward (upper factor), in
+// solve order s = 0 .. nblk-1 (block b = s forward, nblk-1-s backward). With
+// D_s the inverse of diagonal block s, W_s = D_s T(s, s-1) and
+// V_s = D_s T(s, s-2) (both formed once, by launch_diag_inv):
+//   x_s = D_s (rhs_s - sum_{t < s-2} T(s, t) x_t) - V_s x_{s-2} - W_s x_{s-1}.
+// The far sum is cut into chunks of kTiChunk tiles, each done by a helper
+// task that publishes its 64 partial sums; the owner task of block s adds the
+// chunks in order, applies D_s, then V_s x_{s-2} and, once x_{s-1} is known,
+// W_s x_{s-1}: one 64 x 64 product per block stays on the chain, and the far
+// tiles of late blocks (FP64-bound) spread over many SMs.
+//
+// Tasks are drawn by ticket in the order (block 0: owner; block 1: owner;
+// block s: helpers 0 .. h_s - 1, owner), so a task only ever waits for tasks
+// with smaller tickets, which have started. Results announce themselves: X and
+// the partial-sum slots start as an all-ones bit pattern (a NaN that
+// arithmetic does not produce) and a consumer polls the values it needs.
+// The result is a fixed linear map of rhs (the same operations in the same
+// order every call), as GMRES requires.
 constexpr unsigned long long kXUnset = 0xffffffffffffffffull;
+constexpr int kTiChunk = 16;
+
+__host__ __device__ inline int ti_helpers(int s) { return s >= 2 ? (s - 2 + kTiChunk - 1) / kTiChunk : 0; }
+
+static int ti_tasks(int nblk) {
+  int t = 0;
+  for (int s = 0; s < nblk; ++s) t += ti_helpers(s) + 1;
+  return t;
+}
+
+size_t diag_inv_doubles(int n) {
+  const int nblk = (n + kTsBS - 1) / kTsBS;
+  return (size_t)3 * nblk * kTsBS * kTsBS + (size_t)ti_tasks(nblk) * kTsBS;
+}
+
+// poll one announced FP64 value (bounded); false on timeout
+GBLA_DEVINL bool ti_poll(const double* p, uint64_t wait_ns, double* out) {
+  const unsigned long long* px = reinterpret_cast<const unsigned long long*>(p);
+  unsigned long long bits;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(bits) : "l"(px) : "memory");
+  if (bits == kXUnset) {
+    const uint64_t t0 = gbla_now_ns();
+    do {
+      asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(bits) : "l"(px) : "memory");
+      if (gbla_now_ns() - t0 > wait_ns) return false;
+    } while (bits == kXUnset);
+  }
+  *out = __longlong_as_double((long long)bits);
+  return true;
+}
+
+GBLA_DEVINL void ti_announce(double* p, double v) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(bits) : "memory");
+}
+
+// W_s and V_s (CTA (s, k): k = 0 -> W_s = D_s T(s, s-1), k = 1 -> V_s = D_s T(s, s-2)).
+
+template <typename Ts, bool FWD>
+__global__ void __launch_bounds__(256)
+    trsv_wv_kernel(int n, const Ts* __restrict__ T, int ldt, double* __restrict__ Dinv) {
+  extern __shared__ double wv_smem[];
+  double* Ds = wv_smem;                                                  // column-major D_s
+  double (*Tt)[kTsBS + 1] = reinterpret_cast<double (*)[kTsBS + 1]>(wv_smem + kTsBS * kTsBS);  // T(b, q)
+  const int nblk = (n + kTsBS - 1) / kTsBS;
+  const int s = blockIdx.x, k = blockIdx.y;
+  const int sp = s - 1 - k;
+  if (sp < 0) return;
+  const int b = FWD ? s : nblk - 1 - s, q = FWD ? sp : nblk - 1 - sp;
+  const int r0 = b * kTsBS, c0 = q * kTsBS;
+  const int nr = min(kTsBS, n - r0), nc = min(kTsBS, n - c0);
+  const double* D = Dinv + (size_t)b * kTsBS * kTsBS;
+  for (int i = threadIdx.x; i < kTsBS * kTsBS; i += blockDim.x) {
+    Ds[i] = D[i];
+    const int rr = i & 63, jj = i >> 6;
+    Tt[rr][jj] = (rr < nr && jj < nc) ? (double)T[(r0 + rr) + (size_t)(c0 + jj) * ldt] : 0.0;
+  }
+  __syncthreads();
+  double* out = Dinv + (size_t)(1 + k) * nblk * kTsBS * kTsBS + (size_t)b * kTsBS * kTsBS;
+  const int r = threadIdx.x & 63, g = threadIdx.x >> 6;
+  for (int jj = g * 16; jj < g * 16 + 16; ++jj) {
+    double a0 = 0.0, a1 = 0.0;
+#pragma unroll 8
+    for (int kk = 0; kk < kTsBS; kk += 2) {
+      a0 = fma(Ds[r + kTsBS * kk], Tt[kk][jj], a0);
+      a1 = fma(Ds[r + kTsBS * (kk + 1)], Tt[kk + 1][jj], a1);
+    }
+    out[r + kTsBS * jj] = a0 + a1;
+  }
+}
 
 template <typename Ts, bool FWD>
 __global__ void __launch_bounds__(256)
@@ -278,107 +379,163 @@ __global__ void __launch_bounds__(256)
                     const double* __restrict__ rhs, double* X, unsigned* ticket, int* info,
                     uint64_t wait_ns) {
   extern __shared__ double smd[];
-  double* dinv = smd;                  // 64 x 64, column-major
-  double* xq = dinv + kTsBS * kTsBS;   // 64
-  double* part = xq + kTsBS;           // 4 x 64
-  double* rb = part + 4 * kTsBS;       // 64: this block's right-hand side
+  double* xq = smd;                    // 64: the x values of the current step
+  double* part = xq + kTsBS;           // 4 x 64 partial sums
+  double* dv = part + 4 * kTsBS;       // 64: owner's running vector
+  double* mat = dv + kTsBS;            // 64 x 64: D_s, then V_s, then W_s (owner)
   __shared__ int s_t, s_abort;
   const int tid = threadIdx.x;
   const int nblk = (n + kTsBS - 1) / kTsBS;
+  const size_t nbsq = (size_t)kTsBS * kTsBS;
+  double* P = const_cast<double*>(Dinv) + 3 * (size_t)nblk * nbsq;  // partial-sum slots
   if (tid == 0) {
     s_t = (int)atomicAdd(ticket, 1u);
     s_abort = 0;
   }
   __syncthreads();
-  const int t_ord = s_t;
-  if (t_ord >= nblk) return;
-  const int b = FWD ? t_ord : nblk - 1 - t_ord;
+  int t = s_t;
+  // ticket -> (block s, helper c or owner), first ticket of block s
+  int s = 0, first = 0;
+  for (; s < nblk; ++s) {
+    const int cnt = ti_helpers(s) + 1;
+    if (t < first + cnt) break;
+    first += cnt;
+  }
+  if (s >= nblk) return;
+  const int c = t - first;
+  const bool owner = c == ti_helpers(s);
+  const int b = FWD ? s : nblk - 1 - s;
   const int r0 = b * kTsBS;
   const int nr = min(kTsBS, n - r0);
   const int r = tid & 63, g = tid >> 6;
 
-  // the inverse of the diagonal block and the right-hand side, needed last, are staged first
-  const double* Db = Dinv + (size_t)b * kTsBS * kTsBS;
-  for (int idx = tid; idx < kTsBS * kTsBS; idx += blockDim.x) dinv[idx] = Db[idx];
-  if (tid < kTsBS) rb[tid] = tid < nr ? rhs[r0 + tid] : 0.0;
-
-  auto load = [&](int st, Ts (&v)[16]) {
-    const int q = FWD ? st : nblk - 1 - st;
-    const int c0 = q * kTsBS;
-    const int nc = min(kTsBS, n - c0);
-    const Ts* base = T + (r0 + r) + (size_t)c0 * ldt;
+  // y = sum over solve-order blocks s' in [lo, hi) of T(s, s') x_{s'}, into part
+  // (thread (r, g): row r, columns g + 4i of each tile); the tile of the next
+  // block is loaded while the current one waits for its x
+  auto far_sum = [&](int lo, int hi) -> bool {
+    auto load = [&](int sp, Ts (&v)[16]) {
+      const int q = FWD ? sp : nblk - 1 - sp;
+      const int c0 = q * kTsBS;
+      const int nc = min(kTsBS, n - c0);
+      const Ts* base = T + (r0 + r) + (size_t)c0 * ldt;
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const int jj = g + 4 * i;
-      v[i] = (r < nr && jj < nc) ? base[(size_t)jj * ldt] : (Ts)0;
+      for (int i = 0; i < 16; ++i) {
+        const int jj = g + 4 * i;
+        v[i] = (r < nr && jj < nc) ? base[(size_t)jj * ldt] : (Ts)0;
+      }
+    };
+    double a0 = 0.0, a1 = 0.0;
+    Ts cur[16];
+    if (lo < hi) load(lo, cur);
+    for (int sp = lo; sp < hi; ++sp) {
+      const int q = FWD ? sp : nblk - 1 - sp;
+      const int c0 = q * kTsBS;
+      const int nc = min(kTsBS, n - c0);
+      Ts nxt[16];
+      if (sp + 1 < hi) load(sp + 1, nxt);
+      if (tid < kTsBS) {
+        double v = 0.0;
+        if (tid < nc && !ti_poll(X + c0 + tid, wait_ns, &v)) s_abort = 1;
+        xq[tid] = v;
+      }
+      __syncthreads();
+      if (s_abort) return false;
+#pragma unroll
+      for (int i = 0; i < 16; i += 2) {
+        a0 = fma((double)cur[i], xq[g + 4 * i], a0);
+        a1 = fma((double)cur[i + 1], xq[g + 4 * (i + 1)], a1);
+      }
+      if (sp + 1 < hi) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) cur[i] = nxt[i];
+      }
+      __syncthreads();  // xq is rewritten next step
     }
+    part[g * kTsBS + r] = a0 + a1;
+    __syncthreads();
+    return true;
   };
-  double a0 = 0.0, a1 = 0.0;
-  Ts cur[16];
-  if (t_ord > 0) load(0, cur);
-  for (int st = 0; st < t_ord; ++st) {
-    const int q = FWD ? st : nblk - 1 - st;
+  // part (4 x 64) -> one value per row, fixed order
+  auto row_sum = [&](int rr) {
+    return (part[rr] + part[kTsBS + rr]) + (part[2 * kTsBS + rr] + part[3 * kTsBS + rr]);
+  };
+  // part <- M (64 x 64, column-major, in mat) times xq
+  auto mat_vec = [&]() {
+    double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+    for (int j = g * 16; j < g * 16 + 16; j += 2) {
+      a0 = fma(mat[r + kTsBS * j], xq[j], a0);
+      a1 = fma(mat[r + kTsBS * (j + 1)], xq[j + 1], a1);
+    }
+    part[g * kTsBS + r] = a0 + a1;
+    __syncthreads();
+  };
+  auto load_mat = [&](const double* M) {
+    for (int i = tid; i < kTsBS * kTsBS; i += blockDim.x) mat[i] = M[i];
+  };
+  auto wait_x = [&](int sp) -> bool {  // xq <- x of solve-order block sp
+    const int q = FWD ? sp : nblk - 1 - sp;
     const int c0 = q * kTsBS;
     const int nc = min(kTsBS, n - c0);
-    Ts nxt[16];
-    if (st + 1 < t_ord) load(st + 1, nxt);
     if (tid < kTsBS) {
       double v = 0.0;
-      if (tid < nc) {
-        const unsigned long long* px = reinterpret_cast<const unsigned long long*>(X + c0 + tid);
-        unsigned long long bits;
-        asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(bits) : "l"(px) : "memory");
-        if (bits == kXUnset) {
-          const uint64_t t0 = gbla_now_ns();
-          do {
-            asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(bits) : "l"(px) : "memory");
-            if (gbla_now_ns() - t0 > wait_ns) {
-              s_abort = 1;
-              break;
-            }
-          } while (bits == kXUnset);
-        }
-        v = __longlong_as_double((long long)bits);
-      }
+      if (tid < nc && !ti_poll(X + c0 + tid, wait_ns, &v)) s_abort = 1;
       xq[tid] = v;
     }
     __syncthreads();
-    if (s_abort) {
+    return s_abort == 0;
+  };
+
+  if (!owner) {
+    // helper: the far tiles of chunk c, published in slot t
+    const int lo = c * kTiChunk, hi = min(lo + kTiChunk, s - 2);
+    if (!far_sum(lo, hi)) {
       if (tid == 0) gbla_flag_timeout(info);
       return;
     }
-#pragma unroll
-    for (int i = 0; i < 16; i += 2) {
-      a0 = fma((double)cur[i], xq[g + 4 * i], a0);
-      a1 = fma((double)cur[i + 1], xq[g + 4 * (i + 1)], a1);
-    }
-    if (st + 1 < t_ord) {
-#pragma unroll
-      for (int i = 0; i < 16; ++i) cur[i] = nxt[i];
-    }
-    __syncthreads();  // xq is rewritten next step
+    if (tid < kTsBS) ti_announce(P + (size_t)t * kTsBS + tid, row_sum(tid));
+    return;
   }
-  part[g * kTsBS + r] = a0 + a1;
-  __syncthreads();
+  // owner of block s: rhs minus the helpers' chunks, in order
+  load_mat(Dinv + (size_t)b * nbsq);
   if (tid < kTsBS) {
-    const double sum = (part[tid] + part[kTsBS + tid]) + (part[2 * kTsBS + tid] + part[3 * kTsBS + tid]);
-    xq[tid] = tid < nr ? rb[tid] - sum : 0.0;
+    double acc = tid < nr ? rhs[r0 + tid] : 0.0;
+    for (int h = 0; h < c; ++h) {
+      double v = 0.0;
+      if (!ti_poll(P + (size_t)(first + h) * kTsBS + tid, wait_ns, &v)) s_abort = 1;
+      acc -= v;
+    }
+    xq[tid] = tid < nr ? acc : 0.0;
   }
   __syncthreads();
-  // x_b = Dinv_b * rhs (column-major inverse)
-  double y0 = 0.0, y1 = 0.0;
-#pragma unroll
-  for (int j = g * 16; j < g * 16 + 16; j += 2) {
-    y0 = fma(dinv[r + kTsBS * j], xq[j], y0);
-    y1 = fma(dinv[r + kTsBS * (j + 1)], xq[j + 1], y1);
+  if (s_abort) {
+    if (tid == 0) gbla_flag_timeout(info);
+    return;
   }
-  part[g * kTsBS + r] = y0 + y1;
+  mat_vec();  // D_s (rhs_s - far)
+  if (tid < kTsBS) dv[tid] = row_sum(tid);
   __syncthreads();
-  if (tid < nr) {
-    const double xv = (part[tid] + part[kTsBS + tid]) + (part[2 * kTsBS + tid] + part[3 * kTsBS + tid]);
-    const unsigned long long bits = (unsigned long long)__double_as_longlong(xv);
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(X + r0 + tid), "l"(bits) : "memory");
+  if (s >= 2) {
+    load_mat(Dinv + nblk * nbsq * 2 + (size_t)b * nbsq);  // V_s
+    if (!wait_x(s - 2)) {
+      if (tid == 0) gbla_flag_timeout(info);
+      return;
+    }
+    mat_vec();
+    if (tid < kTsBS) dv[tid] -= row_sum(tid);
+    __syncthreads();
   }
+  if (s >= 1) {
+    load_mat(Dinv + nblk * nbsq + (size_t)b * nbsq);  // W_s
+    if (!wait_x(s - 1)) {
+      if (tid == 0) gbla_flag_timeout(info);
+      return;
+    }
+    mat_vec();
+    if (tid < kTsBS) dv[tid] -= row_sum(tid);
+    __syncthreads();
+  }
+  if (tid < nr) ti_announce(X + r0 + tid, dv[tid]);
 }
 
 template <typename Ts>
@@ -387,27 +544,29 @@ cudaError_t launch_trsv_inv(bool lower, int n, const Ts* T, int ldt, const doubl
                             cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const int nblk = (n + kTsBS - 1) / kTsBS;
-  // One CTA per SM: the late blocks of the chain are bound by the SM's FP64
-  // rate, which two resident blocks would share. Asking for more than half
-  // of an SM's shared memory keeps a second CTA off the SM; the blocks that do
-  // not fit start as the early ones finish (in ticket order, so every block a
-  // CTA waits for has started before it).
+  const int tasks = ti_tasks(nblk);
+  // One CTA per SM: the FP64 rate of an SM is what a block's chain step and
+  // the far tiles are bound by, and two resident CTAs would share it. Asking
+  // for more than half of an SM's shared memory keeps a second CTA off the SM.
   const DeviceProps& dp = device_props();
-  size_t smem = sizeof(double) * ((size_t)kTsBS * kTsBS + kTsBS + 4 * kTsBS + kTsBS);
+  size_t smem = sizeof(double) * ((size_t)kTsBS * kTsBS + 6 * kTsBS);
   if (dp.smem_optin > 2 * smem) smem = dp.smem_optin / 2 + 1024;
   cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(X, 0xff, sizeof(double) * (size_t)n, s);
   if (e != cudaSuccess) return e;
+  double* P = const_cast<double*>(Dinv) + (size_t)3 * nblk * kTsBS * kTsBS;
+  e = cudaMemsetAsync(P, 0xff, sizeof(double) * (size_t)tasks * kTsBS, s);
+  if (e != cudaSuccess) return e;
   const uint64_t wait_ns = wait_timeout_ns();
   if (lower) {
     e = ensure_dyn_smem(trsv_inv_kernel<Ts, true>, smem);
     if (e != cudaSuccess) return e;
-    trsv_inv_kernel<Ts, true><<<nblk, 256, smem, s>>>(n, T, ldt, Dinv, rhs, X, flags, info, wait_ns);
+    trsv_inv_kernel<Ts, true><<<tasks, 256, smem, s>>>(n, T, ldt, Dinv, rhs, X, flags, info, wait_ns);
   } else {
     e = ensure_dyn_smem(trsv_inv_kernel<Ts, false>, smem);
     if (e != cudaSuccess) return e;
-    trsv_inv_kernel<Ts, false><<<nblk, 256, smem, s>>>(n, T, ldt, Dinv, rhs, X, flags, info, wait_ns);
+    trsv_inv_kernel<Ts, false><<<tasks, 256, smem, s>>>(n, T, ldt, Dinv, rhs, X, flags, info, wait_ns);
   }
   count_launch();
   return cudaGetLastError();
