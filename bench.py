@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--e2e-warmup", type=int, default=1,
                     help="untimed end-to-end steps first (the first copy from freshly pinned "
                          "host buffers maps their pages and runs at a fraction of the link rate)")
+    ap.add_argument("--streams", type=int, default=3,
+                    help="systems of a step solved concurrently, each on its own CUDA stream "
+                         "and host thread (1: one after the other)")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the other workloads (FP64 LU/Cholesky n=8192, batched, autograd)")
     ap.add_argument("--cpu-ksteps", type=int, default=8,
@@ -260,15 +263,63 @@ def run_reference(args, ws, rank):
 
 
 # ---------------------------------------------------------------------- our arm
-def solve_all(api, As, bs, args, F):
-    stats = []
-    for A, b in zip(As, bs):
-        Fk, ipiv, info = api.lu_factor_mixed(A, prec=args.prec, nb=args.nb, F=F)
-        x, st = api.gmresir(A, Fk, ipiv, b, tol=1e-14, inner_tol=1e-8, max_outer=20,
-                            restart_m=args.restart)
-        st["x"] = x
-        stats.append(st)
-    return stats
+def solve_one(api, A, b, args, F):
+    Fk, ipiv, info = api.lu_factor_mixed(A, prec=args.prec, nb=args.nb, F=F)
+    x, st = api.gmresir(A, Fk, ipiv, b, tol=1e-14, inner_tol=1e-8, max_outer=20,
+                        restart_m=args.restart)
+    st["x"] = x
+    return st
+
+
+class Concurrent:
+    """The systems of a step are independent: each is factored and refined on a
+    CUDA stream of its own, issued by a host thread of its own (the refinement
+    reads its convergence test on the host, so one thread per system keeps the
+    other systems' work queued meanwhile). Every stream starts after the work
+    already on the caller's stream, and the caller's stream waits for all of
+    them at the end, so events on the caller's stream bracket the whole step."""
+
+    def __init__(self, k):
+        self.device = torch.cuda.current_device()
+        self.streams = [torch.cuda.Stream() for _ in range(k)]
+
+    def run(self, jobs):
+        """Job i runs on stream i mod k; the jobs of one stream run in order on
+        one host thread."""
+        main = torch.cuda.current_stream()
+        k = len(self.streams)
+        out = [None] * len(jobs)
+        err = []
+
+        def work(t):
+            try:
+                torch.cuda.set_device(self.device)
+                s = self.streams[t]
+                s.wait_stream(main)
+                with torch.cuda.stream(s):
+                    for i in range(t, len(jobs), k):
+                        out[i] = jobs[i]()
+            except BaseException as e:  # re-raised on the caller's thread
+                err.append(e)
+
+        th = [threading.Thread(target=work, args=(t,)) for t in range(min(k, len(jobs)))]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        for s in self.streams:
+            main.wait_stream(s)
+        if err:
+            raise err[0]
+        return out
+
+
+def solve_all(api, As, bs, args, Fs, conc=None):
+    if conc is None:
+        return [solve_one(api, A, b, args, Fs[0]) for A, b in zip(As, bs)]
+    jobs = [(lambda A=A, b=b, F=Fs[i % len(Fs)]: solve_one(api, A, b, args, F))
+            for i, (A, b) in enumerate(zip(As, bs))]
+    return conc.run(jobs)
 
 
 def run_ours(args, ws, rank):
@@ -278,14 +329,18 @@ def run_ours(args, ws, rank):
     n = args.n
     dev = "cuda"
     As, bs, x_true = make_workload(n, dev)
-    F = torch.empty_strided((n, n), (1, n), dtype=torch.float32, device=dev)
     nsys = len(As)
+    nconc = max(1, min(args.streams, nsys))
+    Fs = [torch.empty_strided((n, n), (1, n), dtype=torch.float32, device=dev) for _ in range(nconc)]
+    conc = Concurrent(nconc) if nconc > 1 else None
 
-    # warm-up; the first warm-up step records every kernel group to find the dominant one
+    # warm-up; the first warm-up step runs the systems one after the other and
+    # records every kernel group (a per-group breakdown without overlap) to
+    # find the dominant one
     api.prof_enable(api.KERNEL_KINDS)
     api.prof_reset()
     for w in range(max(args.warmup, 1)):
-        solve_all(api, As, bs, args, F)
+        solve_all(api, As, bs, args, Fs, None if w == 0 else conc)
         if w == 0:
             torch.cuda.synchronize()
             per_kind = {k: api.prof_read(k) for k in api.KERNEL_KINDS}
@@ -306,7 +361,7 @@ def run_ours(args, ws, rank):
     ev0.record()
     all_stats = []
     for _ in range(args.steps):
-        all_stats.append(solve_all(api, As, bs, args, F))
+        all_stats.append(solve_all(api, As, bs, args, Fs, conc))
     ev1.record()
     torch.cuda.synchronize()
     barrier(ws)
@@ -365,17 +420,32 @@ def run_ours(args, ws, rank):
             db[k].copy_(hostb[k], non_blocking=True)
             copied[k].record(copy_s)
 
-    def e2e_step():
+    def e2e_step_serial():
         copy_s.wait_stream(main)  # after the previous step has read the buffers
         fetch(0)
         for k in range(nsys):
             if k + 1 < nsys:
                 fetch(k + 1)
             main.wait_event(copied[k])
-            Fk, ipiv, info = api.lu_factor_mixed(dA[k], prec=args.prec, nb=args.nb, F=F)
+            Fk, ipiv, info = api.lu_factor_mixed(dA[k], prec=args.prec, nb=args.nb, F=Fs[0])
             x, st = api.gmresir(dA[k], Fk, ipiv, db[k], tol=1e-14, max_outer=20,
                                 restart_m=args.restart)
             hx[k].copy_(x, non_blocking=True)
+
+    def e2e_job(k):
+        # on system k's own stream: its inputs in, factor, refine, its x out
+        dA[k].copy_(hostA[k], non_blocking=True)
+        db[k].copy_(hostb[k], non_blocking=True)
+        Fk, ipiv, info = api.lu_factor_mixed(dA[k], prec=args.prec, nb=args.nb, F=Fs[k % nconc])
+        x, st = api.gmresir(dA[k], Fk, ipiv, db[k], tol=1e-14, max_outer=20,
+                            restart_m=args.restart)
+        hx[k].copy_(x, non_blocking=True)
+
+    def e2e_step():
+        if conc is None:
+            e2e_step_serial()
+        else:
+            conc.run([(lambda k=k: e2e_job(k)) for k in range(nsys)])
 
     for _ in range(args.e2e_warmup):
         e2e_step()
@@ -468,6 +538,7 @@ def run_ours(args, ws, rank):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "%s update, f32 factors, f64 refinement" % args.prec, "data": "synthetic",
             "config": bench_config(args, nsys, ws),
+            "concurrent_systems": nconc,
             "roofline": roof,
             "roofline_other_kernels": others,
             "cpu_baseline": cpu,
@@ -560,6 +631,13 @@ def secondary(args, pk):
     fp64_peak = 2 * 8192 ** 3 / (ms * 1e-3) / 1e12
     del a
     out["fp64_dgemm_tflops_measured"] = fp64_peak
+    # the device's own FMA rates (probe kernels of this library): the denominators
+    # of the ALU-bound lines below; DGEMM stays as context
+    api.fma_peak("fp64", iters=1 << 14)
+    fma64 = api.fma_peak("fp64")
+    fma32 = api.fma_peak("fp32")
+    out["fma_peak_tflops_measured"] = {"fp64": fma64, "fp32": fma32,
+                                       "how": "independent FMA chains on every SM, CUDA events"}
     # n = 512, one RHS, x_true = 1
     n = 512
     A = inputs.uniform(n, 0, dev)
@@ -585,6 +663,7 @@ def secondary(args, pk):
     beta = float(api.backward_error(A, X, B).max().item())
     tf = lu_flops(n) / (ms_f * 1e-3) / 1e12
     out["lu_n8192_fp64"] = {"nb": nb, "factor_ms": ms_f, "tflops": tf, "frac_of_fp64_dgemm": tf / fp64_peak,
+                            "frac_of_fp64_fma_peak": tf / fma64,
                             "solve16_ms": ms_s,
                             "solve_gbs": (n * n * 8) / (ms_s * 1e-3) / 1e9, "beta_max": beta}
     del LU, X
@@ -598,6 +677,7 @@ def secondary(args, pk):
     Xc = api.chol_solve(F, Bs)
     tfc = n ** 3 / 3.0 / (ms_c * 1e-3) / 1e12
     out["chol_n8192_fp64"] = {"nb": nbc, "factor_ms": ms_c, "tflops": tfc, "frac_of_fp64_dgemm": tfc / fp64_peak,
+                              "frac_of_fp64_fma_peak": tfc / fma64,
                               "beta_max": float(api.backward_error(S, Xc, Bs).max().item())}
     del S, F, Xc, A, B
     # mixed-precision Cholesky + GMRES-IR against the FP64 Cholesky, SPD n = 16384
@@ -633,6 +713,9 @@ def secondary(args, pk):
                  "beta_max_first512": worst}
         if dt == torch.float64:
             entry["frac_of_fp64_dgemm"] = entry["tflops"] / fp64_peak
+            entry["frac_of_fp64_fma_peak"] = entry["tflops"] / fma64
+        else:
+            entry["frac_of_fp32_fma_peak"] = entry["tflops"] / fma32
         out[name] = entry
         del bl
     # batched Cholesky on SPD systems of the same sizes (A_i^t A_i / n_i + I), FP64
@@ -659,6 +742,7 @@ def secondary(args, pk):
     out["batched_chol_fp64"] = {"systems": len(sizes), "graph_ms": ms_gc, "kernel_ms": kc,
                                 "systems_per_s": len(sizes) / (kc * 1e-3),
                                 "tflops": flops_c / (kc * 1e-3) / 1e12,
+                                "frac_of_fp64_fma_peak": flops_c / (kc * 1e-3) / 1e12 / fma64,
                                 "launch_shape": [bc.threads, bc.ctas_per_sm],
                                 "info_nonzero": int((infoc != 0).sum()), "beta_max_first512": worst}
     del bc, Sp

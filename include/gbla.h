@@ -101,6 +101,18 @@ int gbla_prof_list(int kind, int max_count, double *ms);
 void gbla_set_wait_timeout_ns(uint64_t ns);
 uint64_t gbla_get_wait_timeout_ns(void);
 
+/*
+ * Measured arithmetic rate of the device, for rooflines (the paper has no
+ * counterpart: it quotes no peak). precision 0: FP64 fused multiply-add,
+ * 1: FP32. Runs one untimed and one timed launch of independent FMA chains
+ * filling every SM (`iters` steps of 8 chains per thread; 2 flops per FMA),
+ * timed with CUDA events on `stream`, and writes the rate in TFLOP/s to
+ * *tflops (host pointer). Synchronises with the stream. Returns -1 for a bad
+ * precision, -2 for iters < 1, -3 for a null tflops, GBLA_ERR_CUDA on a
+ * runtime failure.
+ */
+int gbla_fma_peak(int precision, int iters, double *tflops, gbla_stream_t stream);
+
 /* ------------------------------------------------------------------------
  * FP64 LU with partial pivoting (paper section 2; steps a1-a4).
  * Blocked right-looking: each block column of width nb is factored as

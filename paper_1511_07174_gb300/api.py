@@ -402,6 +402,14 @@ def prof_list(kind, max_count=100000):
     return [buf[i] for i in range(c)]
 
 
+def fma_peak(precision="fp64", iters=1 << 16):
+    """Measured FP64 or FP32 fused multiply-add rate of the current device, TFLOP/s."""
+    t = ctypes.c_double(0.0)
+    code = {"fp64": 0, "fp32": 1}[precision]
+    _check("gbla_fma_peak", _lib.load().gbla_fma_peak(code, int(iters), ctypes.byref(t), _stream()))
+    return t.value
+
+
 # ------------------------------------------------------------------ autotuning
 def _tune_nb(kind, n, candidates, run, device, use_cache):
     from . import batched as _b

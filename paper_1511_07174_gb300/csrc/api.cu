@@ -69,7 +69,11 @@ static std::mutex g_prof_mu;
 static unsigned g_prof_mask = 0;
 static std::vector<ProfRec> g_prof_recs;   // recorded pairs, in order
 static std::vector<cudaEvent_t> g_prof_pool;
-static size_t g_prof_open = (size_t)-1;
+// the open record of the calling thread (calls on several host threads
+// interleave), valid while no reset has happened since it was opened
+static thread_local size_t g_prof_open = (size_t)-1;
+static thread_local uint64_t g_prof_open_gen = 0;
+static uint64_t g_prof_gen = 1;
 
 static cudaEvent_t prof_event() {
   if (!g_prof_pool.empty()) {
@@ -89,12 +93,14 @@ void prof_begin(int kind, cudaStream_t s) {
   cudaEventRecord(r.a, s);
   g_prof_recs.push_back(r);
   g_prof_open = g_prof_recs.size() - 1;
+  g_prof_open_gen = g_prof_gen;
 }
 
 void prof_end(int kind, cudaStream_t s) {
   if (!(g_prof_mask & (1u << kind))) return;
   std::lock_guard<std::mutex> lock(g_prof_mu);
-  if (g_prof_open < g_prof_recs.size() && g_prof_recs[g_prof_open].kind == kind)
+  if (g_prof_open_gen == g_prof_gen && g_prof_open < g_prof_recs.size() &&
+      g_prof_recs[g_prof_open].kind == kind)
     cudaEventRecord(g_prof_recs[g_prof_open].b, s);
   g_prof_open = (size_t)-1;
 }
@@ -310,6 +316,7 @@ void gbla_prof_reset(void) {
     g_prof_pool.push_back(r.b);
   }
   g_prof_recs.clear();
+  ++g_prof_gen;
   g_prof_open = (size_t)-1;
 }
 

@@ -297,114 +297,118 @@ GBLA_DEVINL void panel_tail_swaps(Ts* A, int lda, int w, int nleft, int nright, 
   }
 }
 
+// Final sources of the rows touched by kb <= 256 sequential interchanges
+// (row t <-> row p_t for t = 0 .. kb - 1 in order, p_t >= t, rows relative to
+// the block's first row), worked out by the threads t < kb in parallel. With
+// pre(t) the value row t holds just before interchange t:
+//   pre(t) = pre(i) for the last i < t with p_i = t, else row t's own value;
+//   row t ends with pre(t) if p_t = t, else with what row p_t held just
+//   before interchange t: pre(i) for the last i < t with p_i = p_t, else p_t's
+//   own value;
+//   a partner row x >= kb ends with pre(i) for the last interchange i naming it.
+// pre follows the chains t -> i (i < t) to a row that kept its own value,
+// found by pointer jumping (8 rounds cover chains of 256). Every thread of the
+// CTA must call it (it contains barriers); s.p must already hold the p_t.
+struct SwapPlanShared {
+  int p[256];
+  int J[2][256];
+};
+
+// Thread t < kb: *src_b = the row whose original value ends in row t; when t
+// is the last interchange naming a partner row p_t >= kb, *dst_o = p_t and
+// *src_o its source, else *dst_o = -1.
+GBLA_DEVINL void swap_plan(SwapPlanShared& s, int kb, int t, int* src_b, int* dst_o, int* src_o) {
+  int last_to = -1, prev_same = -1;
+  bool later = false;
+  const int pt = t < kb ? s.p[t] : -1;
+  if (t < kb) {
+    for (int i = 0; i < kb; ++i) {
+      const int q = s.p[i];
+      if (i < t) {
+        if (q == t) last_to = i;
+        if (q == pt) prev_same = i;
+      } else if (i > t && q == pt) {
+        later = true;
+      }
+    }
+    s.J[0][t] = last_to < 0 ? t : last_to;
+  }
+  __syncthreads();
+  int cur = 0;
+#pragma unroll 1
+  for (int r = 0; r < 8; ++r) {
+    if (t < kb) s.J[cur ^ 1][t] = s.J[cur][s.J[cur][t]];
+    __syncthreads();
+    cur ^= 1;
+  }
+  *dst_o = -1;
+  if (t < kb) {
+    const int pre_t = s.J[cur][t];
+    *src_b = pt == t ? pre_t : (prev_same >= 0 ? s.J[cur][prev_same] : pt);
+    if (pt >= kb && !later) {
+      *dst_o = pt;
+      *src_o = pre_t;
+    }
+  }
+}
+
 // Interchanges of one outer block (ipiv[0 .. kb), 1-based absolute rows, the
 // block starting at row k0; kb <= 256) applied to columns [0, skip_lo) and
 // [skip_hi, ncols) of the nrows x ncols matrix (LAPACK laswp semantics, in
-// order). Every CTA first works out, once, where each touched row's final
-// value comes from: the slots are the kb rows of the block (slot t = row
-// k0 + t) and, for each partner row below the block, the slot kb + f of the
-// first interchange f that names it; one thread runs the kb exchanges on slot
-// identities in shared memory. Then, 32 columns at a time, the CTA loads the
-// touched rows of its columns into shared memory (the block's rows
-// coalesced, the partner rows one element per column) and writes each
-// touched row back from the slot that holds its final value. Columns are
-// never shared between CTAs; no waits. Pivots outside [row t, nrows) are
-// ignored.
-constexpr int kLbCols = 32;
-constexpr int kLbBatch = 16;  // loads a thread keeps in flight
-
+// order). Every CTA first works out where each touched row's final value
+// comes from (swap_plan): thread t holds at most two (destination, source)
+// pairs, block row t and the partner row its interchange names last. Then,
+// for a tile of columns, each thread loads the sources of its pairs in every
+// column of the tile into registers, the CTA meets at a barrier, and each
+// thread stores them to the destinations: a gather followed by a scatter, one
+// address per element; the block's rows are consecutive lanes. Rows that keep
+// their value are skipped. Columns are never shared between CTAs; no waits.
+// Pivots outside [row t, nrows) are ignored.
 template <typename T>
 __global__ void __launch_bounds__(256)
     laswp_block_kernel(T* __restrict__ A, int lda, int ncols, int nrows, int k0, int kb,
                        const int* __restrict__ ipiv, int skip_lo, int skip_hi) {
-  extern __shared__ double lb_smem[];
-  T* V = reinterpret_cast<T*>(lb_smem);                           // [2 kb][kLbCols + 1]
-  int* s_p = reinterpret_cast<int*>(V + (size_t)2 * kb * (kLbCols + 1));  // kb partner rows (relative)
-  int* s_f = s_p + kb;          // kb: first interchange naming the same outside row, or -1
-  int* s_row = s_f + kb;        // 2 kb: row of each slot (relative), -1 if unused
-  int* s_src = s_row + 2 * kb;  // 2 kb: slot whose old value ends up in this slot
-  int* s_list = s_src + 2 * kb; // 2 kb: the used slots, the block's rows first, in order
-  __shared__ int s_nv;
+  constexpr int LC = sizeof(T) == 4 ? 32 : 16;  // columns per tile
+  __shared__ SwapPlanShared s_plan;
   const int tid = threadIdx.x;
-  const int S = 2 * kb;
-  if (tid == 0) s_nv = kb;
-  for (int j = tid; j < kb; j += blockDim.x) {
-    int p = ipiv[j] - 1 - k0;
-    if (p < j || p >= nrows - k0) p = j;
-    s_p[j] = p;
+  const int R = nrows - k0;
+  if (tid < kb) {
+    int p = ipiv[tid] - 1 - k0;
+    if (p < tid || p >= R) p = tid;
+    s_plan.p[tid] = p;
   }
   __syncthreads();
-  for (int j = tid; j < kb; j += blockDim.x) {
-    const int p = s_p[j];
-    int f = -1;
-    if (p >= kb) {
-      f = j;
-      for (int k = 0; k < j; ++k)
-        if (s_p[k] == p) {
-          f = k;
-          break;
-        }
-    }
-    s_f[j] = f;
-    s_row[j] = j;
-    s_row[kb + j] = (f == j) ? p : -1;
-    s_list[j] = j;
-    if (f == j) s_list[atomicAdd(&s_nv, 1)] = kb + j;
-  }
-  for (int q = tid; q < S; q += blockDim.x) s_src[q] = q;
-  __syncthreads();
-  if (tid == 0) {
-    for (int j = 0; j < kb; ++j) {
-      const int p = s_p[j];
-      const int b = p < kb ? p : kb + s_f[j];
-      const int t = s_src[j];
-      s_src[j] = s_src[b];
-      s_src[b] = t;
-    }
-  }
-  __syncthreads();
-  const int nv = s_nv;
+  int src_b = tid, dst_o = -1, src_o = 0;
+  swap_plan(s_plan, kb, tid, &src_b, &dst_o, &src_o);
+  int dr[2], sr[2];
+  dr[0] = (tid < kb && src_b != tid) ? tid : -1;
+  sr[0] = src_b;
+  dr[1] = dst_o;
+  sr[1] = src_o;
   const int skip = skip_hi - skip_lo;
   const int nfar = ncols - skip;
-  const int ntiles = (nfar + kLbCols - 1) / kLbCols;
-  const int total = nv * kLbCols;
+  const int ntiles = (nfar + LC - 1) / LC;
   T* base = A + k0;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int q0 = tile * kLbCols;
-    // gather: kLbBatch independent loads per thread in flight, then the stores
-    for (int i0 = 0; i0 < total; i0 += 256 * kLbBatch) {
-      T v[kLbBatch];
+    const int q0 = tile * LC;
+    T v[2][LC];
 #pragma unroll
-      for (int u = 0; u < kLbBatch; ++u) {
-        const int idx = i0 + tid + 256 * u;
-        v[u] = (T)0;
-        if (idx < total) {
-          const int c = idx / nv, q = q0 + c;
-          if (q < nfar) {
-            const int col = q < skip_lo ? q : q + skip;
-            v[u] = base[(size_t)col * lda + s_row[s_list[idx - c * nv]]];
-          }
-        }
-      }
+    for (int c = 0; c < LC; ++c) {
+      const int q = q0 + c;
+      const int col = q < skip_lo ? q : q + skip;
 #pragma unroll
-      for (int u = 0; u < kLbBatch; ++u) {
-        const int idx = i0 + tid + 256 * u;
-        if (idx < total) {
-          const int c = idx / nv;
-          V[(size_t)s_list[idx - c * nv] * (kLbCols + 1) + c] = v[u];
-        }
-      }
+      for (int u = 0; u < 2; ++u)
+        if (q < nfar && dr[u] >= 0) v[u][c] = base[(size_t)col * lda + sr[u]];
     }
-    __syncthreads();
-    for (int idx = tid; idx < total; idx += blockDim.x) {
-      const int c = idx / nv, q = q0 + c;
-      if (q < nfar) {
-        const int sl = s_list[idx - c * nv];
-        const int col = q < skip_lo ? q : q + skip;
-        base[(size_t)col * lda + s_row[sl]] = V[(size_t)s_src[sl] * (kLbCols + 1) + c];
-      }
+    __syncthreads();  // every read of the tile's columns before any write
+#pragma unroll
+    for (int c = 0; c < LC; ++c) {
+      const int q = q0 + c;
+      const int col = q < skip_lo ? q : q + skip;
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+        if (q < nfar && dr[u] >= 0) base[(size_t)col * lda + dr[u]] = v[u][c];
     }
-    __syncthreads();
   }
 }
 
@@ -414,21 +418,19 @@ cudaError_t launch_laswp_block(T* A, int lda, int ncols, int nrows, int k0, int 
   const int nfar = ncols - (skip_hi - skip_lo);
   if (nfar <= 0 || kb <= 0) return cudaSuccess;
   if (kb > 256) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)2 * kb * (kLbCols + 1) * sizeof(T) + (size_t)8 * kb * sizeof(int);
-  cudaError_t e = ensure_dyn_smem(laswp_block_kernel<T>, smem);
-  if (e != cudaSuccess) return e;
   const DeviceProps& dp = device_props();
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, laswp_block_kernel<T>, 256, smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, laswp_block_kernel<T>, 256, 0) !=
           cudaSuccess ||
       per_sm < 1) {
     cudaGetLastError();
     per_sm = 1;
   }
-  const int ntiles = (nfar + kLbCols - 1) / kLbCols;
+  constexpr int LC = sizeof(T) == 4 ? 32 : 16;
+  const int ntiles = (nfar + LC - 1) / LC;
   int grid = per_sm * (dp.num_sms > 0 ? dp.num_sms : 1);
   if (grid > ntiles) grid = ntiles;
-  laswp_block_kernel<T><<<grid, 256, smem, s>>>(A, lda, ncols, nrows, k0, kb, ipiv, skip_lo, skip_hi);
+  laswp_block_kernel<T><<<grid, 256, 0, s>>>(A, lda, ncols, nrows, k0, kb, ipiv, skip_lo, skip_hi);
   count_launch();
   return cudaGetLastError();
 }
@@ -445,8 +447,8 @@ template cudaError_t launch_laswp_block<float>(float*, int, int, int, int, int, 
 // c's interchanges (the identity outside the rows they touch), the final value
 // of row q comes from row tau_b(q) = sigma_{b+1}(sigma_{b+2}(...(q))).
 //
-// left_perm_kernel (one CTA): sigma_c is formed by running block c's
-// interchanges, in order, on an identity array in shared memory (one thread);
+// left_perm_kernel (one CTA): sigma_c is formed from block c's interchanges by
+// swap_plan and written into an identity array in shared memory;
 // tau is composed from the last block backwards, tau <- sigma_c o tau, and
 // tau_{c-1} is stored for every block c >= 1 (rows >= k_c; the rest of the
 // row range is not read). Pivots outside [row, n) are ignored, as everywhere.
@@ -454,6 +456,7 @@ __global__ void __launch_bounds__(1024)
     left_perm_kernel(int n, int nb, const int* __restrict__ ipiv, int* __restrict__ tau,
                      int* __restrict__ snaps) {
   extern __shared__ int lp_D[];  // n entries
+  __shared__ SwapPlanShared s_plan;
   const int tid = threadIdx.x;
   for (int q = tid; q < n; q += blockDim.x) {
     lp_D[q] = q;
@@ -463,14 +466,17 @@ __global__ void __launch_bounds__(1024)
   const int nblk = (n + nb - 1) / nb;
   for (int c = nblk - 1; c >= 1; --c) {
     const int k0 = c * nb, kb = min(nb, n - k0);
-    if (tid == 0) {
-      for (int j = 0; j < kb; ++j) {
-        int p = ipiv[k0 + j] - 1;
-        if (p < k0 + j || p >= n) p = k0 + j;
-        const int t = lp_D[k0 + j];
-        lp_D[k0 + j] = lp_D[p];
-        lp_D[p] = t;
-      }
+    if (tid < kb) {
+      int p = ipiv[k0 + tid] - 1 - k0;
+      if (p < tid || p >= n - k0) p = tid;
+      s_plan.p[tid] = p;
+    }
+    __syncthreads();
+    int src_b = tid, dst_o = -1, src_o = 0;
+    swap_plan(s_plan, kb, tid, &src_b, &dst_o, &src_o);
+    if (tid < kb) {
+      lp_D[k0 + tid] = k0 + src_b;
+      if (dst_o >= 0) lp_D[k0 + dst_o] = k0 + src_o;
     }
     __syncthreads();
     int* snap = snaps + (size_t)(c - 1) * n;
@@ -481,11 +487,9 @@ __global__ void __launch_bounds__(1024)
     }
     __syncthreads();
     // back to the identity on the rows block c touched
-    for (int j = tid; j < kb; j += blockDim.x) {
-      int p = ipiv[k0 + j] - 1;
-      if (p < k0 + j || p >= n) p = k0 + j;
-      lp_D[k0 + j] = k0 + j;
-      lp_D[p] = p;
+    if (tid < kb) {
+      lp_D[k0 + tid] = k0 + tid;
+      if (dst_o >= 0) lp_D[k0 + dst_o] = k0 + dst_o;
     }
     __syncthreads();
   }

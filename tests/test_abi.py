@@ -41,6 +41,10 @@ def test_wait_timeout_roundtrip(lib):
 def test_invalid_arguments_rejected_on_host(lib):
     v = ctypes.c_void_p(0)
     assert lib.gbla_lu_factor(-1, v, 1, v, v, 0, v, 0, v) == -1
+    t = ctypes.c_double(0.0)
+    assert lib.gbla_fma_peak(2, 16, ctypes.byref(t), v) == -1
+    assert lib.gbla_fma_peak(0, 0, ctypes.byref(t), v) == -2
+    assert lib.gbla_fma_peak(0, 16, None, v) == -3
     assert lib.gbla_lu_factor(4, v, 4, v, v, 0, v, 0, v) == -2
     fake = ctypes.c_void_p(256)
     assert lib.gbla_lu_factor(4, fake, 3, fake, fake, 0, fake, 0, v) == -3
