@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--streams", type=int, default=3,
                     help="systems of a step solved concurrently, each on its own CUDA stream "
                          "and host thread (1: one after the other)")
+    ap.add_argument("--subst-ctas", type=int, default=0,
+                    help="cap on the CTAs of the refinement's substitution (0: one per SM)")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the other workloads (FP64 LU/Cholesky n=8192, batched, autograd)")
     ap.add_argument("--cpu-ksteps", type=int, default=8,
@@ -330,6 +332,7 @@ def run_ours(args, ws, rank):
     dev = "cuda"
     As, bs, x_true = make_workload(n, dev)
     nsys = len(As)
+    api.set_substitution_ctas(args.subst_ctas)
     nconc = max(1, min(args.streams, nsys))
     Fs = [torch.empty_strided((n, n), (1, n), dtype=torch.float32, device=dev) for _ in range(nconc)]
     conc = Concurrent(nconc) if nconc > 1 else None
@@ -433,9 +436,8 @@ def run_ours(args, ws, rank):
             hx[k].copy_(x, non_blocking=True)
 
     def e2e_job(k):
-        # on system k's own stream: its inputs in, factor, refine, its x out
-        dA[k].copy_(hostA[k], non_blocking=True)
-        db[k].copy_(hostb[k], non_blocking=True)
+        # on system k's own stream, once its inputs are in: factor, refine, x out
+        torch.cuda.current_stream().wait_event(copied[k])
         Fk, ipiv, info = api.lu_factor_mixed(dA[k], prec=args.prec, nb=args.nb, F=Fs[k % nconc])
         x, st = api.gmresir(dA[k], Fk, ipiv, db[k], tol=1e-14, max_outer=20,
                             restart_m=args.restart)
@@ -445,6 +447,11 @@ def run_ours(args, ws, rank):
         if conc is None:
             e2e_step_serial()
         else:
+            # the inputs travel one system after the other on the copy stream
+            # (system 0 first), each system's solve starts once its own are in
+            copy_s.wait_stream(main)
+            for k in range(nsys):
+                fetch(k)
             conc.run([(lambda k=k: e2e_job(k)) for k in range(nsys)])
 
     for _ in range(args.e2e_warmup):
@@ -539,6 +546,7 @@ def run_ours(args, ws, rank):
             "dtype": "%s update, f32 factors, f64 refinement" % args.prec, "data": "synthetic",
             "config": bench_config(args, nsys, ws),
             "concurrent_systems": nconc,
+            "substitution_ctas": args.subst_ctas,
             "roofline": roof,
             "roofline_other_kernels": others,
             "cpu_baseline": cpu,

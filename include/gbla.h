@@ -102,6 +102,19 @@ void gbla_set_wait_timeout_ns(uint64_t ns);
 uint64_t gbla_get_wait_timeout_ns(void);
 
 /*
+ * Cap on the number of CTAs of the refinement's preconditioner substitution
+ * (the inverted-diagonal-block forward and back solves inside
+ * gbla_gmresir_solve*, gbla_chol_gmresir_solve_nrhs, gbla_gmres_solve and
+ * gbla_bicgstab_solve). The substitution runs as a persistent grid of at most
+ * one CTA per SM that draws its tasks in order; a cap leaves the other SMs
+ * free for work on other streams (several systems solved concurrently). The
+ * result does not depend on the cap. 0 (default): one CTA per SM.
+ * Process-wide. Returns -1 for ctas < 0.
+ */
+int gbla_set_substitution_ctas(int ctas);
+int gbla_get_substitution_ctas(void);
+
+/*
  * Measured arithmetic rate of the device, for rooflines (the paper has no
  * counterpart: it quotes no peak). precision 0: FP64 fused multiply-add,
  * 1: FP32. Runs one untimed and one timed launch of independent FMA chains

@@ -402,6 +402,16 @@ def prof_list(kind, max_count=100000):
     return [buf[i] for i in range(c)]
 
 
+def set_substitution_ctas(ctas):
+    """Cap the CTAs of the refinement's substitution (0: one per SM); the
+    result does not depend on it."""
+    _check("gbla_set_substitution_ctas", _lib.load().gbla_set_substitution_ctas(int(ctas)))
+
+
+def get_substitution_ctas():
+    return int(_lib.load().gbla_get_substitution_ctas())
+
+
 def fma_peak(precision="fp64", iters=1 << 16):
     """Measured FP64 or FP32 fused multiply-add rate of the current device, TFLOP/s."""
     t = ctypes.c_double(0.0)

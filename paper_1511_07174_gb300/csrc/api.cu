@@ -17,6 +17,8 @@ namespace gbla {
 
 static uint64_t g_wait_ns = 2000000000ull;
 uint64_t wait_timeout_ns() { return g_wait_ns; }
+static std::atomic<int> g_subst_ctas{0};
+int substitution_ctas() { return g_subst_ctas.load(std::memory_order_relaxed); }
 
 const DeviceProps& device_props() {
   static DeviceProps props[64];
@@ -358,6 +360,12 @@ int gbla_prof_list(int kind, int max_count, double* ms) {
 }
 
 void gbla_set_wait_timeout_ns(uint64_t ns) { g_wait_ns = ns; }
+int gbla_set_substitution_ctas(int ctas) {
+  if (ctas < 0) return -1;
+  g_subst_ctas.store(ctas, std::memory_order_relaxed);
+  return GBLA_OK;
+}
+int gbla_get_substitution_ctas(void) { return substitution_ctas(); }
 uint64_t gbla_get_wait_timeout_ns(void) { return g_wait_ns; }
 
 // ---------------------------------------------------------------------------

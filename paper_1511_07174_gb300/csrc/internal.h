@@ -10,6 +10,7 @@ namespace gbla {
 
 // ---- process-wide settings ------------------------------------------------
 uint64_t wait_timeout_ns();
+int substitution_ctas();  // cap on the refinement substitution's persistent grid (0: one per SM)
 
 struct DeviceProps {
   int device = -1;

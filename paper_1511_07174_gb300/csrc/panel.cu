@@ -1057,6 +1057,11 @@ GBLA_DEVINL void cl_sync() {
                    : "memory");
 }
 
+// Correctly rounded reciprocal (the value 1 / x rounds to, as the division
+// gives it, in fewer instructions).
+GBLA_DEVINL float rcp_rn(float x) { return __frcp_rn(x); }
+GBLA_DEVINL double rcp_rn(double x) { return __drcp_rn(x); }
+
 template <typename Ts, int NT, int RPT>
 __global__ void __launch_bounds__(NT, 1)
     panel_cluster_kernel(Ts* __restrict__ A, int lda, int m, int row0, int* __restrict__ ipiv,
@@ -1216,7 +1221,7 @@ __global__ void __launch_bounds__(NT, 1)
       }
       // each lane forms the reciprocal of its candidate's pivot while the
       // warp reduces the keys; the winner's is then broadcast
-      const Ts qr = qv != (Ts)0 ? (Ts)1 / qv : (Ts)0;
+      const Ts qr = qv != (Ts)0 ? rcp_rn(qv) : (Ts)0;
       Key g = q;
       warp_merge_redux(g);
       const unsigned bal = __ballot_sync(0xffffffffu, lane < CL && q.same(g));

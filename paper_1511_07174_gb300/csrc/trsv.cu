@@ -388,6 +388,11 @@ __global__ void __launch_bounds__(256)
   const int nblk = (n + kTsBS - 1) / kTsBS;
   const size_t nbsq = (size_t)kTsBS * kTsBS;
   double* P = const_cast<double*>(Dinv) + 3 * (size_t)nblk * nbsq;  // partial-sum slots
+  // Persistent: each CTA draws tickets until they run out. A task only waits
+  // for tasks with smaller tickets, drawn earlier by CTAs that are running, so
+  // the grid may be smaller than the number of tasks.
+  for (;;) {
+  __syncthreads();  // the previous task's shared memory is no longer read
   if (tid == 0) {
     s_t = (int)atomicAdd(ticket, 1u);
     s_abort = 0;
@@ -494,7 +499,7 @@ __global__ void __launch_bounds__(256)
       return;
     }
     if (tid < kTsBS) ti_announce(P + (size_t)t * kTsBS + tid, row_sum(tid));
-    return;
+    continue;
   }
   // owner of block s: rhs minus the helpers' chunks, in order
   load_mat(Dinv + (size_t)b * nbsq);
@@ -536,6 +541,7 @@ __global__ void __launch_bounds__(256)
     __syncthreads();
   }
   if (tid < nr) ti_announce(X + r0 + tid, dv[tid]);
+  }
 }
 
 template <typename Ts>
@@ -548,9 +554,15 @@ cudaError_t launch_trsv_inv(bool lower, int n, const Ts* T, int ldt, const doubl
   // One CTA per SM: the FP64 rate of an SM is what a block's chain step and
   // the far tiles are bound by, and two resident CTAs would share it. Asking
   // for more than half of an SM's shared memory keeps a second CTA off the SM.
+  // The grid is persistent (at most one CTA per SM, fewer when capped by
+  // gbla_set_substitution_ctas), leaving the other SMs to concurrent work.
   const DeviceProps& dp = device_props();
   size_t smem = sizeof(double) * ((size_t)kTsBS * kTsBS + 6 * kTsBS);
   if (dp.smem_optin > 2 * smem) smem = dp.smem_optin / 2 + 1024;
+  int grid = dp.num_sms > 0 ? dp.num_sms : 1;
+  const int cap = substitution_ctas();
+  if (cap > 0 && cap < grid) grid = cap;
+  if (grid > tasks) grid = tasks;
   cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(X, 0xff, sizeof(double) * (size_t)n, s);
@@ -562,11 +574,11 @@ cudaError_t launch_trsv_inv(bool lower, int n, const Ts* T, int ldt, const doubl
   if (lower) {
     e = ensure_dyn_smem(trsv_inv_kernel<Ts, true>, smem);
     if (e != cudaSuccess) return e;
-    trsv_inv_kernel<Ts, true><<<tasks, 256, smem, s>>>(n, T, ldt, Dinv, rhs, X, flags, info, wait_ns);
+    trsv_inv_kernel<Ts, true><<<grid, 256, smem, s>>>(n, T, ldt, Dinv, rhs, X, flags, info, wait_ns);
   } else {
     e = ensure_dyn_smem(trsv_inv_kernel<Ts, false>, smem);
     if (e != cudaSuccess) return e;
-    trsv_inv_kernel<Ts, false><<<tasks, 256, smem, s>>>(n, T, ldt, Dinv, rhs, X, flags, info, wait_ns);
+    trsv_inv_kernel<Ts, false><<<grid, 256, smem, s>>>(n, T, ldt, Dinv, rhs, X, flags, info, wait_ns);
   }
   count_launch();
   return cudaGetLastError();

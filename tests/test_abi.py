@@ -38,6 +38,14 @@ def test_wait_timeout_roundtrip(lib):
     lib.gbla_set_wait_timeout_ns(old)
 
 
+def test_substitution_ctas_roundtrip(lib):
+    old = lib.gbla_get_substitution_ctas()
+    assert lib.gbla_set_substitution_ctas(-1) == -1
+    assert lib.gbla_set_substitution_ctas(24) == 0
+    assert lib.gbla_get_substitution_ctas() == 24
+    assert lib.gbla_set_substitution_ctas(old) == 0
+
+
 def test_invalid_arguments_rejected_on_host(lib):
     v = ctypes.c_void_p(0)
     assert lib.gbla_lu_factor(-1, v, 1, v, v, 0, v, 0, v) == -1

@@ -209,3 +209,24 @@ def test_solve_mixed_several_rhs():
         assert sts[j]["converged"]
         assert oracle.backward_error(An, X[:, j].cpu().numpy(), B[:, j].cpu().numpy())[0] <= 1e-14
 
+
+
+@pytest.mark.parametrize("n", [600, 2100])
+def test_substitution_cap_gives_the_same_result(n):
+    """The refinement's substitution is a persistent grid drawing its tasks in
+    order; capping its CTAs (here below the number of tasks) changes which CTA
+    runs a task, not the operations: the refined x and the iteration counts
+    must be identical."""
+    A, b = _haar_system(n, 1e4)
+    Ad, bd = A.to(DEV), b.to(DEV)
+    F, ipiv, info = api.lu_factor_mixed(Ad, prec="fp16x3", nb=128)
+    x0, st0 = api.gmresir(Ad, F, ipiv, bd, tol=1e-14, max_outer=10)
+    old = api.get_substitution_ctas()
+    try:
+        api.set_substitution_ctas(3)
+        x1, st1 = api.gmresir(Ad, F, ipiv, bd, tol=1e-14, max_outer=10)
+    finally:
+        api.set_substitution_ctas(old)
+    assert torch.equal(x0, x1)
+    assert (st0["outer"], st0["inner"]) == (st1["outer"], st1["inner"])
+    assert st0["converged"]
