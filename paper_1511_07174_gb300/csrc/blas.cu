@@ -557,33 +557,43 @@ cudaError_t launch_copy_d2f(const double* A, int lda, float* F, int ldf, int m, 
 }
 
 // ----------------------------------------------------------------------------
-// perm from sequential interchanges: (P v)[i] = v[perm[i]]. The pivots are
-// staged in shared memory by the whole block (when both arrays fit), then one
-// thread applies the n swaps in order; every access of that loop is to shared
-// memory. For very large n the arrays stay in global memory.
-__global__ void ipiv_to_perm_kernel(int n, const int* __restrict__ ipiv, int* __restrict__ perm,
-                                    int use_smem) {
+// perm from sequential interchanges: (P v)[i] = v[perm[i]]. One CTA takes the
+// interchanges 256 at a time: swap_plan gives, in parallel, where each row
+// touched by the chunk gets its value from, and the CTA applies that map to
+// the running permutation (every read before any write). The permutation
+// lives in shared memory when it fits, else in perm itself.
+__global__ void __launch_bounds__(1024)
+    ipiv_to_perm_kernel(int n, const int* __restrict__ ipiv, int* __restrict__ perm, int use_smem) {
   extern __shared__ int sp[];
+  __shared__ SwapPlanShared s_plan;
   int* p = use_smem ? sp : perm;
-  const int* piv = use_smem ? sp + n : ipiv;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    p[i] = i;
-    if (use_smem) sp[n + i] = ipiv[i];
-  }
+  const int t = threadIdx.x;
+  for (int i = t; i < n; i += blockDim.x) p[i] = i;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int j = 0; j < n; ++j) {
-      const int k = piv[j] - 1;
-      if (k != j && k > j && k < n) {  // out-of-range pivots are ignored
-        const int t = p[j];
-        p[j] = p[k];
-        p[k] = t;
-      }
+  for (int c0 = 0; c0 < n; c0 += 256) {
+    const int kb = min(256, n - c0);
+    if (t < kb) {
+      int q = ipiv[c0 + t] - 1 - c0;
+      if (q < t || q >= n - c0) q = t;  // out-of-range pivots are ignored
+      s_plan.p[t] = q;
     }
+    __syncthreads();
+    int src_b = t, dst_o = -1, src_o = 0;
+    swap_plan(s_plan, kb, t, &src_b, &dst_o, &src_o);
+    int vb = 0, vo = 0;
+    if (t < kb) {
+      vb = p[c0 + src_b];
+      if (dst_o >= 0) vo = p[c0 + src_o];
+    }
+    __syncthreads();
+    if (t < kb) {
+      p[c0 + t] = vb;
+      if (dst_o >= 0) p[c0 + dst_o] = vo;
+    }
+    __syncthreads();
   }
-  __syncthreads();
   if (use_smem)
-    for (int i = threadIdx.x; i < n; i += blockDim.x) perm[i] = p[i];
+    for (int i = t; i < n; i += blockDim.x) perm[i] = p[i];
 }
 
 __global__ void iota_kernel(int n, int* __restrict__ perm) {
@@ -598,8 +608,8 @@ cudaError_t launch_ipiv_to_perm(int n, const int* ipiv, int* perm, cudaStream_t 
     return cudaGetLastError();
   }
   const DeviceProps& dp = device_props();
-  const size_t bytes = (size_t)2 * n * sizeof(int);
-  const int use_smem = bytes + 1024 <= dp.smem_optin ? 1 : 0;
+  const size_t bytes = (size_t)n * sizeof(int);
+  const int use_smem = bytes + sizeof(SwapPlanShared) + 1024 <= dp.smem_optin ? 1 : 0;
   if (use_smem) {
     cudaError_t ea = ensure_dyn_smem(ipiv_to_perm_kernel, bytes);
     if (ea != cudaSuccess) return ea;

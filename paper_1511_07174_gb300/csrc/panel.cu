@@ -297,61 +297,6 @@ GBLA_DEVINL void panel_tail_swaps(Ts* A, int lda, int w, int nleft, int nright, 
   }
 }
 
-// Final sources of the rows touched by kb <= 256 sequential interchanges
-// (row t <-> row p_t for t = 0 .. kb - 1 in order, p_t >= t, rows relative to
-// the block's first row), worked out by the threads t < kb in parallel. With
-// pre(t) the value row t holds just before interchange t:
-//   pre(t) = pre(i) for the last i < t with p_i = t, else row t's own value;
-//   row t ends with pre(t) if p_t = t, else with what row p_t held just
-//   before interchange t: pre(i) for the last i < t with p_i = p_t, else p_t's
-//   own value;
-//   a partner row x >= kb ends with pre(i) for the last interchange i naming it.
-// pre follows the chains t -> i (i < t) to a row that kept its own value,
-// found by pointer jumping (8 rounds cover chains of 256). Every thread of the
-// CTA must call it (it contains barriers); s.p must already hold the p_t.
-struct SwapPlanShared {
-  int p[256];
-  int J[2][256];
-};
-
-// Thread t < kb: *src_b = the row whose original value ends in row t; when t
-// is the last interchange naming a partner row p_t >= kb, *dst_o = p_t and
-// *src_o its source, else *dst_o = -1.
-GBLA_DEVINL void swap_plan(SwapPlanShared& s, int kb, int t, int* src_b, int* dst_o, int* src_o) {
-  int last_to = -1, prev_same = -1;
-  bool later = false;
-  const int pt = t < kb ? s.p[t] : -1;
-  if (t < kb) {
-    for (int i = 0; i < kb; ++i) {
-      const int q = s.p[i];
-      if (i < t) {
-        if (q == t) last_to = i;
-        if (q == pt) prev_same = i;
-      } else if (i > t && q == pt) {
-        later = true;
-      }
-    }
-    s.J[0][t] = last_to < 0 ? t : last_to;
-  }
-  __syncthreads();
-  int cur = 0;
-#pragma unroll 1
-  for (int r = 0; r < 8; ++r) {
-    if (t < kb) s.J[cur ^ 1][t] = s.J[cur][s.J[cur][t]];
-    __syncthreads();
-    cur ^= 1;
-  }
-  *dst_o = -1;
-  if (t < kb) {
-    const int pre_t = s.J[cur][t];
-    *src_b = pt == t ? pre_t : (prev_same >= 0 ? s.J[cur][prev_same] : pt);
-    if (pt >= kb && !later) {
-      *dst_o = pt;
-      *src_o = pre_t;
-    }
-  }
-}
-
 // Interchanges of one outer block (ipiv[0 .. kb), 1-based absolute rows, the
 // block starting at row k0; kb <= 256) applied to columns [0, skip_lo) and
 // [skip_hi, ncols) of the nrows x ncols matrix (LAPACK laswp semantics, in

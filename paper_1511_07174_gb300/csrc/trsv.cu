@@ -551,14 +551,14 @@ cudaError_t launch_trsv_inv(bool lower, int n, const Ts* T, int ldt, const doubl
   if (n <= 0) return cudaSuccess;
   const int nblk = (n + kTsBS - 1) / kTsBS;
   const int tasks = ti_tasks(nblk);
-  // One CTA per SM: the FP64 rate of an SM is what a block's chain step and
-  // the far tiles are bound by, and two resident CTAs would share it. Asking
-  // for more than half of an SM's shared memory keeps a second CTA off the SM.
-  // The grid is persistent (at most one CTA per SM, fewer when capped by
-  // gbla_set_substitution_ctas), leaving the other SMs to concurrent work.
+  // The grid is persistent: as many CTAs as SMs (fewer when capped by
+  // gbla_set_substitution_ctas), which the scheduler spreads one per SM, so
+  // the FP64 units of an SM, which a block's chain step and the far tiles are
+  // bound by, are not shared between two of them. Each CTA asks for the
+  // shared memory it uses and no more, so kernels on other streams can share
+  // an SM with a CTA that is waiting on the chain.
   const DeviceProps& dp = device_props();
-  size_t smem = sizeof(double) * ((size_t)kTsBS * kTsBS + 6 * kTsBS);
-  if (dp.smem_optin > 2 * smem) smem = dp.smem_optin / 2 + 1024;
+  const size_t smem = sizeof(double) * ((size_t)kTsBS * kTsBS + 6 * kTsBS);
   int grid = dp.num_sms > 0 ? dp.num_sms : 1;
   const int cap = substitution_ctas();
   if (cap > 0 && cap < grid) grid = cap;
