@@ -349,7 +349,13 @@ def run_ours(args, ws, rank):
             per_kind = {k: api.prof_read(k) for k in api.KERNEL_KINDS}
             api.prof_reset()
             api.prof_enable([])
-    dominant = max(per_kind, key=lambda k: per_kind[k][1])
+    # the dominant group by held SM time (duration x SMs held: a cluster panel
+    # holds its 16 SMs, every other kernel group the whole GPU): with the
+    # systems concurrent, that is what bounds a step
+    nsms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    sm_ms = {k: v[1] * (16 if k == "panel" else nsms) for k, v in per_kind.items()}
+    dominant = max(sm_ms, key=lambda k: sm_ms[k])
+    fma64 = api.fma_peak("fp64")
 
     # timed region
     api.prof_enable([dominant])
@@ -489,10 +495,13 @@ def run_ours(args, ws, rank):
                             "each of its 32 interchanges read + written in the other nb - 32 columns "
                             "of its outer block")
     elif dominant == "trsv":
-        alg = trsv_algorithmic_bytes(n, 4) * dom_count
-        achieved = alg / (dom_ms * 1e-3) / 1e9
-        peak, bound, unit = pk.get("hbm_gbs"), "hbm", "GB/s"
-        per_launch_units = "triangle of the FP32 factor read once + vector"
+        # FP64 arithmetic on the FP32 factor: n(n+1)/2 multiply-adds per solve
+        alg = n * (n + 1.0) * dom_count
+        achieved = alg / (dom_ms * 1e-3) / 1e12
+        peak, bound, unit = fma64, "alu", "TFLOP/s"
+        src = "measured (this build's FP64 FMA probe on this GPU)"
+        per_launch_units = ("one triangular solve: n(n+1)/2 FP64 multiply-adds on the FP32 factor "
+                            "(2 flops each); its bytes: the triangle read once, n(n+1)/2 x 4 B")
     else:
         alg = None
         achieved, peak, bound, unit = None, pk.get("hbm_gbs"), "hbm", "GB/s"
@@ -519,15 +528,28 @@ def run_ours(args, ws, rank):
                        "unit": "GB/s", "frac": ach / pk.get("hbm_gbs") if pk.get("hbm_gbs") else None,
                        "algorithmic_units": "FP32 triangle read once + vectors, per solve",
                        "note": "FP64 arithmetic of the late blocks and the block chain bound it"})
+    if dominant != "panel" and per_kind.get("panel", (0, 0.0))[1] > 0:
+        cnt, ms_p = per_kind["panel"]
+        ach = panel_algorithmic_bytes(n, 4, args.nb) * nsys / (ms_p * 1e-3) / 1e9
+        others.append({"kernel": "panel", "bound": "hbm", "achieved": ach, "peak": pk.get("hbm_gbs"),
+                       "unit": "GB/s", "frac": ach / pk.get("hbm_gbs") if pk.get("hbm_gbs") else None,
+                       "algorithmic_units": "slab read + written once plus the interchanged rows of "
+                                            "its outer block, per launch",
+                       "note": "latency-bound: 32 dependent pivot rounds per launch on 16 SMs"})
     roof = {"kernel": dominant, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
             "frac": (achieved / peak) if (achieved and peak) else None, "traffic": None,
             "peak_source": src, "launch_groups": dom_count, "ms_in_timed_region": dom_ms,
             "algorithmic_units": per_launch_units}
-    prof_path = os.path.join(ROOT, "profiles", "traffic.json")
+    roof["held_sm_ms_first_warmup_step"] = {k: round(v, 1) for k, v in sm_ms.items() if v > 0}
+    prof_path = os.path.join(ROOT, "profiles", "traffic_per_launch.txt")
     if os.path.exists(prof_path):
         with open(prof_path) as f:
-            tr = json.load(f)
-        roof["traffic"] = tr.get(dominant)
+            for ln in f:
+                f_ = ln.split()
+                if len(f_) >= 3 and not ln.startswith("#") and f_[0] == dominant and int(f_[1]) == n:
+                    roof["traffic"] = float(f_[2])
+                    roof["traffic_unit"] = "bytes per launch"
+                    roof["traffic_source"] = " ".join(f_[3:])
 
     # bounded CPU baseline: the oracle on the first k elimination steps of one system
     cpu = None
