@@ -115,6 +115,22 @@ int gbla_set_substitution_ctas(int ctas);
 int gbla_get_substitution_ctas(void);
 
 /*
+ * Look-ahead in the blocked LU factorisations (gbla_lu_factor,
+ * gbla_lu_factor_mixed, gbla_lu_factor_static; paper section 2, delayed
+ * updating rescheduled): when on, each trailing update is split into the
+ * next outer block's columns and the rest; the next block's panels are then
+ * factored on a high-priority stream of the library's own while the rest of
+ * the update runs on the caller's stream (the persistent tensor-core update
+ * leaves the panel's 16 SMs free), and the caller's stream waits for them
+ * before the next block's interchanges. The factors are bit-for-bit the same.
+ * The streams and events are created on first use (one set per concurrent
+ * call) and kept until the process exits. 0 (default): off. Process-wide.
+ * Returns -1 for a value other than 0 or 1.
+ */
+int gbla_set_lookahead(int on);
+int gbla_get_lookahead(void);
+
+/*
  * Measured arithmetic rate of the device, for rooflines (the paper has no
  * counterpart: it quotes no peak). precision 0: FP64 fused multiply-add,
  * 1: FP32. Runs one untimed and one timed launch of independent FMA chains

@@ -56,6 +56,8 @@ _SIGS = {
     "gbla_fma_peak": ([_i, _i, ctypes.POINTER(_d), _vp], _i),
     "gbla_set_substitution_ctas": ([_i], _i),
     "gbla_get_substitution_ctas": ([], _i),
+    "gbla_set_lookahead": ([_i], _i),
+    "gbla_get_lookahead": ([], _i),
     "gbla_lu_factor_workspace": ([_i, _i], _sz),
     "gbla_lu_factor": ([_i, _vp, _i, _vp, _vp, _i, _vp, _sz, _vp], _i),
     "gbla_lu_factor_static": ([_i, _vp, _i, _vp, _vp, _i, _vp], _i),

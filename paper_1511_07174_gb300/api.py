@@ -412,6 +412,15 @@ def get_substitution_ctas():
     return int(_lib.load().gbla_get_substitution_ctas())
 
 
+def set_lookahead(on):
+    """Factor the next outer block's panels during the trailing update (same factors)."""
+    _check("gbla_set_lookahead", _lib.load().gbla_set_lookahead(1 if on else 0))
+
+
+def get_lookahead():
+    return bool(_lib.load().gbla_get_lookahead())
+
+
 def fma_peak(precision="fp64", iters=1 << 16):
     """Measured FP64 or FP32 fused multiply-add rate of the current device, TFLOP/s."""
     t = ctypes.c_double(0.0)

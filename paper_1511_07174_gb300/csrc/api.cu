@@ -19,6 +19,9 @@ static uint64_t g_wait_ns = 2000000000ull;
 uint64_t wait_timeout_ns() { return g_wait_ns; }
 static std::atomic<int> g_subst_ctas{0};
 int substitution_ctas() { return g_subst_ctas.load(std::memory_order_relaxed); }
+static std::atomic<int> g_lookahead{0};
+bool lookahead_enabled() { return g_lookahead.load(std::memory_order_relaxed) != 0; }
+constexpr int kClusterSms = 16;  // SMs of the panel's thread-block cluster
 
 const DeviceProps& device_props() {
   static DeviceProps props[64];
@@ -157,6 +160,45 @@ int api_cuda_status(cudaError_t e, const char* what, const char* file, int line)
 
 static bool aligned256(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 255) == 0; }
 
+// Look-ahead resources: a high-priority stream and two events, taken from a
+// process-wide pool for the duration of one factorisation (several host
+// threads may factor at once, each with its own set).
+struct LookAhead {
+  int device = -1;
+  cudaStream_t hp = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+static std::mutex g_la_mu;
+static std::vector<LookAhead> g_la_pool;
+
+static cudaError_t lookahead_acquire(LookAhead* out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  {
+    std::lock_guard<std::mutex> lock(g_la_mu);
+    for (size_t i = 0; i < g_la_pool.size(); ++i)
+      if (g_la_pool[i].device == dev) {
+        *out = g_la_pool[i];
+        g_la_pool.erase(g_la_pool.begin() + (long)i);
+        return cudaSuccess;
+      }
+  }
+  LookAhead r;
+  r.device = dev;
+  int lo = 0, hi = 0;
+  if ((e = cudaDeviceGetStreamPriorityRange(&lo, &hi)) != cudaSuccess) return e;
+  if ((e = cudaStreamCreateWithPriority(&r.hp, cudaStreamNonBlocking, hi)) != cudaSuccess) return e;
+  if ((e = cudaEventCreateWithFlags(&r.fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+  if ((e = cudaEventCreateWithFlags(&r.join, cudaEventDisableTiming)) != cudaSuccess) return e;
+  *out = r;
+  return cudaSuccess;
+}
+static void lookahead_release(const LookAhead& r) {
+  std::lock_guard<std::mutex> lock(g_la_mu);
+  g_la_pool.push_back(r);
+}
+
 // ----------------------------------------------------------------------------
 // Blocked right-looking LU over a generic storage type. Outer blocks of width
 // nb; inside each, inner panels of width kPanelWidth factored by the panel
@@ -165,6 +207,13 @@ static bool aligned256(const void* p) { return (reinterpret_cast<uintptr_t>(p) &
 // restricted to the outer block (one fused launch). After the outer block:
 // its interchanges on every other column (one launch), the U row block and
 // the trailing update.
+//
+// Look-ahead (when enabled): the trailing update is split into the next
+// outer block's columns and the rest. Once the first part is done, the next
+// block's panels are factored on a high-priority stream while the rest of the
+// update runs on the caller's stream on all SMs but 16 (the panel's cluster);
+// the caller's stream then waits for the panels. Every element receives the
+// same operations in the same order as without look-ahead.
 static size_t lu_work_layout(Carver& c, int n, int nb, int prec, LuWork* w) {
   double* slots = c.take<double>(panel_slots_doubles());
   const size_t li = left_perm_ints(n, nb);
@@ -201,64 +250,114 @@ cudaError_t blocked_lu(int n, Ts* A, int lda, int* ipiv, int* info, int nb, int 
   unsigned* inner_ctr = reinterpret_cast<unsigned*>(w.slots + kPanelExchangeDoubles);
   // the columns left of each block get its interchanges at the end when possible
   const bool defer_left = w.left != nullptr && left_deferred_fits<Ts>(n, nb);
+  const bool tensor = prec_is_tensor(prec);
   cudaError_t e;
-  for (int k0 = 0; k0 < n; k0 += nb) {
-    const int kb = std::min(nb, n - k0);
+  // the panels of outer block [k0, k0 + kb) and the inner updates, on stream st
+  auto panels = [&](int k0, int kb, cudaStream_t st) -> cudaError_t {
+    cudaError_t e;
     for (int j0 = k0; j0 < k0 + kb; j0 += kPanelWidth) {
       const int jb = std::min(kPanelWidth, k0 + kb - j0);
       // the panel launch also applies its interchanges to the rest of the outer block
-      PROF(KK_PANEL, s, launch_panel<Ts>(A + j0 + (size_t)j0 * lda, lda, n - j0, jb, j0, ipiv + j0, info,
-                                         w.slots, (unsigned)(j0 / kPanelWidth), j0 - k0,
-                                         k0 + kb - j0 - jb, s));
-      if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
+      PROF(KK_PANEL, st, launch_panel<Ts>(A + j0 + (size_t)j0 * lda, lda, n - j0, jb, j0, ipiv + j0, info,
+                                          w.slots, (unsigned)(j0 / kPanelWidth), j0 - k0,
+                                          k0 + kb - j0 - jb, st));
+      if (e != cudaSuccess) return e;
       const int nrest = k0 + kb - j0 - jb;
       if (nrest > 0 && jb == kPanelWidth) {
         // U12 of the panel and the update of the rest of the outer block, one launch
-        PROF(KK_GEMM_SIMT, s, launch_inner_update<Ts>(n - j0 - jb, nrest, A + j0 + (size_t)j0 * lda, lda,
-                                                      inner_ctr, s));
-        if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
+        PROF(KK_GEMM_SIMT, st, launch_inner_update<Ts>(n - j0 - jb, nrest, A + j0 + (size_t)j0 * lda, lda,
+                                                       inner_ctr, st));
+        if (e != cudaSuccess) return e;
       } else if (nrest > 0) {
-        PROF(KK_TRSM, s, (launch_trsm_lunit<Ts, Tc_trsm>(A + j0 + (size_t)j0 * lda, lda,
-                                           A + j0 + (size_t)(j0 + jb) * lda, lda, jb, nrest, 0,
-                                           nullptr, 0, nullptr, s)));
-        if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
-        PROF(KK_GEMM_SIMT, s, launch_gemm_simt<Ts>(n - j0 - jb, nrest, jb, (Ts)-1, A + (j0 + jb) + (size_t)j0 * lda,
-                                 lda, A + j0 + (size_t)(j0 + jb) * lda, lda, false, (Ts)1,
-                                 A + (j0 + jb) + (size_t)(j0 + jb) * lda, lda, false, s));
-        if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
+        PROF(KK_TRSM, st, (launch_trsm_lunit<Ts, Tc_trsm>(A + j0 + (size_t)j0 * lda, lda,
+                                            A + j0 + (size_t)(j0 + jb) * lda, lda, jb, nrest, 0,
+                                            nullptr, 0, nullptr, st)));
+        if (e != cudaSuccess) return e;
+        PROF(KK_GEMM_SIMT, st, launch_gemm_simt<Ts>(n - j0 - jb, nrest, jb, (Ts)-1, A + (j0 + jb) + (size_t)j0 * lda,
+                                  lda, A + j0 + (size_t)(j0 + jb) * lda, lda, false, (Ts)1,
+                                  A + (j0 + jb) + (size_t)(j0 + jb) * lda, lda, false, st));
+        if (e != cudaSuccess) return e;
       }
     }
+    return cudaSuccess;
+  };
+  // trailing update of block [k0, k0 + kb) restricted to the columns
+  // [k0 + kb + c0, k0 + kb + c0 + nc) (all nt rows below the block)
+  auto update = [&](int k0, int kb, int c0, int nc, int grid_cap, cudaStream_t st) -> cudaError_t {
+    cudaError_t e;
+    const int nt = n - k0 - kb;
+    if (tensor) {
+      if constexpr (sizeof(Ts) == 4) {
+        const size_t eb = prec == GBLA_PREC_TF32 ? 4 : 2;
+        const void* Bk = static_cast<const char*>(w.Bk) + (size_t)c0 * w.ldk * eb;
+        PROF(KK_GEMM_TC, st, launch_gemm_tc(prec_mma_kind(prec), nt, nc, prec_kmult(prec) * kb, w.Ak, w.ldk, Bk,
+                                            w.ldk, w.eA, w.eB + c0,
+                                            reinterpret_cast<float*>(A + (k0 + kb) + (size_t)(k0 + kb + c0) * lda),
+                                            lda, info, false, st, grid_cap));
+        return e;
+      } else {
+        return cudaErrorInvalidValue;
+      }
+    }
+    PROF(KK_GEMM_SIMT, st, launch_gemm_simt<Ts>(nt, nc, kb, (Ts)-1, A + (k0 + kb) + (size_t)k0 * lda, lda,
+                                                A + k0 + (size_t)(k0 + kb + c0) * lda, lda, false, (Ts)1,
+                                                A + (k0 + kb) + (size_t)(k0 + kb + c0) * lda, lda, false, st));
+    return e;
+  };
+  const DeviceProps& dp = device_props();
+  const bool la_on = lookahead_enabled() && n > 2 * nb && dp.num_sms > 32;
+  LookAhead la;
+  if (la_on) {
+    e = lookahead_acquire(&la);
+    if (e != cudaSuccess) { record_error(e, "look-ahead resources", __LINE__); return e; }
+  }
+  cudaError_t status = cudaSuccess;
+  bool have_panels = false;  // the current block's panels were done during the previous update
+  for (int k0 = 0; k0 < n && status == cudaSuccess; k0 += nb) {
+    const int kb = std::min(nb, n - k0);
+    if (!have_panels) {
+      e = panels(k0, kb, s);
+      if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); status = e; break; }
+    }
+    have_panels = false;
     // the block's interchanges on the columns right of it (the U row block
     // and the trailing update below read the interchanged rows) and, unless
     // deferred, on the columns left of it
     PROF(KK_LASWP, s, launch_laswp_block<Ts>(A, lda, n, n, k0, kb, ipiv + k0, defer_left ? 0 : k0,
                                              k0 + kb, s));
-    if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
+    if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); status = e; break; }
     const int nt = n - k0 - kb;
     if (nt <= 0) continue;
-    const bool tensor = prec_is_tensor(prec);
     PROF(KK_TRSM, s, (launch_trsm_lunit<Ts, Tc_trsm>(A + k0 + (size_t)k0 * lda, lda, A + k0 + (size_t)(k0 + kb) * lda,
                                        lda, kb, nt, tensor ? prec : 0, w.Bk, w.ldk, w.eB, s)));
-    if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
+    if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); status = e; break; }
     if (tensor) {
       if constexpr (sizeof(Ts) == 4) {
         PROF(KK_CONVERT, s, launch_convert_rows(reinterpret_cast<const float*>(A + (k0 + kb) + (size_t)k0 * lda), lda,
                                 nt, kb, prec, w.Ak, w.ldk, w.eA, false, s));
-        if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
-        PROF(KK_GEMM_TC, s, launch_gemm_tc(prec_mma_kind(prec), nt, nt, prec_kmult(prec) * kb, w.Ak, w.ldk, w.Bk, w.ldk, w.eA, w.eB,
-                           reinterpret_cast<float*>(A + (k0 + kb) + (size_t)(k0 + kb) * lda), lda,
-                           info, false, s));
-        if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
-      } else {
-        return cudaErrorInvalidValue;
+        if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); status = e; break; }
       }
+    }
+    const int nb_next = std::min(nb, nt);
+    if (la_on && nt > nb_next) {
+      // the next block's columns first, then its panels on the high-priority
+      // stream while the rest of the update runs here
+      e = update(k0, kb, 0, nb_next, 0, s);
+      if (e == cudaSuccess) e = cudaEventRecord(la.fork, s);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(la.hp, la.fork, 0);
+      if (e == cudaSuccess) e = panels(k0 + kb, nb_next, la.hp);
+      if (e == cudaSuccess) e = cudaEventRecord(la.join, la.hp);
+      if (e == cudaSuccess) e = update(k0, kb, nb_next, nt - nb_next, dp.num_sms - kClusterSms, s);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, la.join, 0);
+      if (e != cudaSuccess) { record_error(e, "blocked_lu look-ahead", __LINE__); status = e; break; }
+      have_panels = true;
     } else {
-      PROF(KK_GEMM_SIMT, s, launch_gemm_simt<Ts>(nt, nt, kb, (Ts)-1, A + (k0 + kb) + (size_t)k0 * lda, lda,
-                               A + k0 + (size_t)(k0 + kb) * lda, lda, false, (Ts)1,
-                               A + (k0 + kb) + (size_t)(k0 + kb) * lda, lda, false, s));
-      if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
+      e = update(k0, kb, 0, nt, 0, s);
+      if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); status = e; break; }
     }
   }
+  if (la_on) lookahead_release(la);
+  if (status != cudaSuccess) return status;
   if (defer_left) {
     PROF(KK_LASWP, s, launch_left_interchanges<Ts>(A, lda, n, nb, ipiv, w.left, s));
     if (e != cudaSuccess) { record_error(e, "blocked_lu step", __LINE__); return e; }
@@ -366,6 +465,12 @@ int gbla_set_substitution_ctas(int ctas) {
   return GBLA_OK;
 }
 int gbla_get_substitution_ctas(void) { return substitution_ctas(); }
+int gbla_set_lookahead(int on) {
+  if (on != 0 && on != 1) return -1;
+  g_lookahead.store(on, std::memory_order_relaxed);
+  return GBLA_OK;
+}
+int gbla_get_lookahead(void) { return g_lookahead.load(std::memory_order_relaxed); }
 uint64_t gbla_get_wait_timeout_ns(void) { return g_wait_ns; }
 
 // ---------------------------------------------------------------------------

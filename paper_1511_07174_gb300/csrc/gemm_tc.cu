@@ -178,6 +178,13 @@ GBLA_DEVINL void tma_reduce_add_2d(const CUtensorMap* map, int x, int y, uint32_
       "r"(x), "r"(y), "r"(src)
       : "memory");
 }
+// Bring a box of C into L2 ahead of its reduction (no completion to wait for).
+GBLA_DEVINL void tma_prefetch_2d(const CUtensorMap* map, int x, int y) {
+  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y)
+               : "memory");
+}
 GBLA_DEVINL void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 GBLA_DEVINL void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 GBLA_DEVINL void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
@@ -264,6 +271,14 @@ __global__ void __launch_bounds__(kPsThreads, 1)
         int ti, tj;
         tile_coords(t, args.tilesM, args.lower, ti, tj);
         const int m0 = ti * kTcBM, n0 = tj * kTcBN;
+        if constexpr (TMAC) {
+          // the tile's C into L2 while its MMAs run, so that the epilogue's
+          // reductions find it there (8 boxes of 32 rows x 64 columns)
+#pragma unroll
+          for (int r = 0; r < kTcBM; r += 32)
+#pragma unroll
+            for (int c = 0; c < kTcBN; c += 64) tma_prefetch_2d(&tmC, m0 + r, n0 + c);
+        }
         for (int kb = 0; kb < KB; ++kb, ++it) {
           const int st = it % kPsStages;
           const uint32_t ph = (uint32_t)((it / kPsStages) & 1);
@@ -324,6 +339,22 @@ __global__ void __launch_bounds__(kPsThreads, 1)
     for (int t = blockIdx.x; t < args.ntiles; t += gridDim.x, ++i) {
       const int b = i & 1;
       const uint32_t u = (uint32_t)(i >> 1);
+      // the tile's scales are loaded before its accumulator is waited for, so
+      // that their latency hides behind the MMAs: this lane's row, and the
+      // columns c_lo + lane and c_lo + 32 + lane of this warp's half
+      int ti, tj;
+      tile_coords(t, args.tilesM, args.lower, ti, tj);
+      const int m0 = ti * kTcBM, n0 = tj * kTcBN;
+      const int row = m0 + eg * 32 + lane;
+      const bool rok = row < args.M;
+      const float sa = (rok && args.eA) ? pow2f(-args.eA[row]) : 1.0f;
+      const int ncol = min(kTcBN, args.N - n0);
+      float sbh[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int col = c_lo + 32 * h + lane;
+        sbh[h] = (args.eB && col < ncol) ? pow2f(-__ldg(args.eB + n0 + col)) : 1.0f;
+      }
       int bad = 0;
       if (lane == 0) bad = (!mbar_wait_bounded(bar_tfull + 8 * b, u & 1u, args.wait_ns)) || *s_fail;
       bad = __shfl_sync(0xffffffffu, bad, 0);
@@ -332,13 +363,6 @@ __global__ void __launch_bounds__(kPsThreads, 1)
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      int ti, tj;
-      tile_coords(t, args.tilesM, args.lower, ti, tj);
-      const int m0 = ti * kTcBM, n0 = tj * kTcBN;
-      const int row = m0 + eg * 32 + lane;
-      const bool rok = row < args.M;
-      const float sa = (rok && args.eA) ? pow2f(-args.eA[row]) : 1.0f;
-      const int ncol = min(kTcBN, args.N - n0);
       if constexpr (TMAC) {
         // this warp's staging area: 64 columns x 32 rows, column-major
         const int wi = warp - 2;
@@ -350,11 +374,12 @@ __global__ void __launch_bounds__(kPsThreads, 1)
         for (int cb = c_lo; cb < c_lo + kTcBN / 2; cb += 16) {
           uint32_t v[16];
           tmem_ld16(tmem + (uint32_t)(b * kTcBN) + ((uint32_t)(eg * 32) << 16) + (uint32_t)cb, v);
-          const float my_sb = (args.eB && lane < 16 && cb + lane < ncol) ? pow2f(-__ldg(args.eB + n0 + cb + lane)) : 1.0f;
+          const int q = cb - c_lo;  // 0, 16, 32, 48
+          const float my_sb = q < 32 ? sbh[0] : sbh[1];
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
-            const float sb = __shfl_sync(0xffffffffu, my_sb, j);
-            st[(cb - c_lo + j) * 32 + lane] = -((__uint_as_float(v[j]) * sa) * sb);
+            const float sb = __shfl_sync(0xffffffffu, my_sb, (q & 31) + j);
+            st[(q + j) * 32 + lane] = -((__uint_as_float(v[j]) * sa) * sb);
           }
         }
         fence_proxy_async_smem();
@@ -373,10 +398,11 @@ __global__ void __launch_bounds__(kPsThreads, 1)
       for (int cb = c_lo; cb < c_lo + kTcBN / 2; cb += 16) {
         uint32_t v[16];
         tmem_ld16(tmem + (uint32_t)(b * kTcBN) + ((uint32_t)(eg * 32) << 16) + (uint32_t)cb, v);
-        const float my_sb = (args.eB && lane < 16 && cb + lane < ncol) ? pow2f(-__ldg(args.eB + n0 + cb + lane)) : 1.0f;
+        const int q = cb - c_lo;
+        const float my_sb = q < 32 ? sbh[0] : sbh[1];
         float sbv[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) sbv[j] = __shfl_sync(0xffffffffu, my_sb, j);
+        for (int j = 0; j < 16; ++j) sbv[j] = __shfl_sync(0xffffffffu, my_sb, (q & 31) + j);
         if (rok) {
           float cv[16];
 #pragma unroll
@@ -454,7 +480,7 @@ static bool encode_kmajor(CUtensorMap* map, int kind, const void* ptr, int K, in
 
 cudaError_t launch_gemm_tc(int kind, int M, int N, int K, const void* Ak, int ldak, const void* Bk,
                            int ldbk, const int* eA, const int* eB, float* C, int ldc, int* info,
-                           bool lower, cudaStream_t s) {
+                           bool lower, cudaStream_t s, int grid_cap) {
   if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
   if (lower && M != N) return cudaErrorInvalidValue;
   const int elem = kind == GBLA_PREC_TF32 ? 4 : 2;
@@ -469,6 +495,7 @@ cudaError_t launch_gemm_tc(int kind, int M, int N, int K, const void* Ak, int ld
   PsArgs a{M, N, K, tilesM, ntiles, lower ? 1 : 0, C, ldc, eA, eB, info, wait_timeout_ns()};
   const DeviceProps& dp = device_props();
   int grid = dp.num_sms > 0 ? dp.num_sms : 1;
+  if (grid_cap > 0 && grid > grid_cap) grid = grid_cap;
   if (grid > a.ntiles) grid = a.ntiles;
   // the TMA reduction needs a 16-byte aligned C and a column stride that is a
   // multiple of 16 bytes; otherwise the epilogue updates C with plain loads/stores

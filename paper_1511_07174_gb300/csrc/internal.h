@@ -11,6 +11,7 @@ namespace gbla {
 // ---- process-wide settings ------------------------------------------------
 uint64_t wait_timeout_ns();
 int substitution_ctas();  // cap on the refinement substitution's persistent grid (0: one per SM)
+bool lookahead_enabled();  // factor the next outer block's panels during the trailing update
 
 struct DeviceProps {
   int device = -1;
@@ -170,9 +171,11 @@ cudaError_t launch_copy_d2f(const double* A, int lda, float* F, int ldf, int m, 
 // A_k: M rows of K elements (row stride ldak elements), B_k: N rows of K (ldbk).
 // lower (M == N): only the 128 x 128 tiles on or below the diagonal (the
 // diagonal tiles are updated whole, upper part included).
+// grid_cap > 0: at most that many persistent CTAs (the rest of the GPU stays
+// free for work on another stream).
 cudaError_t launch_gemm_tc(int kind, int M, int N, int K, const void* Ak, int ldak,
                            const void* Bk, int ldbk, const int* eA, const int* eB, float* C,
-                           int ldc, int* info, bool lower, cudaStream_t s);
+                           int ldc, int* info, bool lower, cudaStream_t s, int grid_cap = 0);
 
 // ---- triangular solves ------------------------------------------------------
 // uplo_lower: the stored triangle; trans: solve with its transpose; unit: unit diagonal.

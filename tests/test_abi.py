@@ -46,6 +46,13 @@ def test_substitution_ctas_roundtrip(lib):
     assert lib.gbla_set_substitution_ctas(old) == 0
 
 
+def test_lookahead_roundtrip(lib):
+    old = lib.gbla_get_lookahead()
+    assert lib.gbla_set_lookahead(2) == -1
+    assert lib.gbla_set_lookahead(1) == 0 and lib.gbla_get_lookahead() == 1
+    assert lib.gbla_set_lookahead(old) == 0
+
+
 def test_invalid_arguments_rejected_on_host(lib):
     v = ctypes.c_void_p(0)
     assert lib.gbla_lu_factor(-1, v, 1, v, v, 0, v, 0, v) == -1
