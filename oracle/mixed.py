@@ -98,7 +98,7 @@ def lowprec_product(L21, U12, prec):
     raise ValueError(prec)
 
 
-def lu_lowprec(A, nb, prec, with_gap=False, force_ipiv=None):
+def lu_lowprec(A, nb, prec, with_gap=False, force_ipiv=None, ko=None):
     """Blocked right-looking GEPP of fp32(A). Returns (W packed L\\U as FP32 values in float64,
     ipiv int32 1-based, info), and with with_gap=True also the smallest relative
     gap (|a_p| - |a_second|) / |a_p| between the two largest candidates of any
@@ -110,46 +110,75 @@ def lu_lowprec(A, nb, prec, with_gap=False, force_ipiv=None):
     (another implementation's choices); the extra return value is then the
     largest relative shortfall (max|a| - |a_forced|) / max|a| of a forced pivot
     against the column's largest candidate (0.0 when every forced pivot is a
-    largest candidate)."""
+    largest candidate).
+
+    ko (a multiple of nb): two-level delayed updating (paper section 2's k
+    rank-1 updates replaced by one rank-k update, applied twice). Within a
+    super-block of ko columns every nb-block is factored and updates only the
+    super-block's own columns; then the super-block's rows of the columns
+    right of it are solved block by block (each block's FP32 substitution,
+    then the update of the super-block's rows below it in the update
+    precision), and the rows below the super-block receive one rank-ko update
+    with operand scales over the whole ko-long slivers."""
     W = to_fp32(np.array(A, dtype=np.float64, order="F"))
     n = W.shape[0]
     ipiv = np.zeros(n, dtype=np.int32)
     info = 0
     gap = 1.0
     slack = 0.0
-    for k0 in range(0, n, nb):
-        k1 = min(k0 + nb, n)
-        # 1. panel, unblocked, FP64 arithmetic rounded to FP32
-        for j in range(k0, k1):
-            col = np.abs(W[j:, j])
-            if force_ipiv is not None:
-                p = int(force_ipiv[j]) - 1
-                if col.max() > 0:
-                    slack = max(slack, float((col.max() - col[p - j]) / col.max()))
-            else:
-                p = j + int(np.argmax(col))          # first maximum -> lowest index
-            if col.shape[0] > 1 and col.max() > 0:
-                top2 = np.sort(col)[-2:]
-                gap = min(gap, float((top2[1] - top2[0]) / top2[1]))
-            ipiv[j] = p + 1
-            if W[p, j] != 0.0:
-                if p != j:
-                    W[[j, p], :] = W[[p, j], :]
-                W[j + 1:, j] = to_fp32(W[j + 1:, j] / W[j, j])
-            elif info == 0:
-                info = j + 1
-            if j + 1 < k1:
-                W[j + 1:, j + 1:k1] = to_fp32(W[j + 1:, j + 1:k1]
-                                             - np.outer(W[j + 1:, j], W[j, j + 1:k1]))
-        if k1 >= n:
+    ko = nb if ko is None else ko
+    if ko % nb != 0:
+        raise ValueError("ko must be a multiple of nb")
+    for K0 in range(0, n, ko):
+        E = min(K0 + ko, n)
+        for k0 in range(K0, E, nb):
+            k1 = min(k0 + nb, E)
+            # 1. panel, unblocked, FP64 arithmetic rounded to FP32
+            for j in range(k0, k1):
+                col = np.abs(W[j:, j])
+                if force_ipiv is not None:
+                    p = int(force_ipiv[j]) - 1
+                    if col.max() > 0:
+                        slack = max(slack, float((col.max() - col[p - j]) / col.max()))
+                else:
+                    p = j + int(np.argmax(col))          # first maximum -> lowest index
+                if col.shape[0] > 1 and col.max() > 0:
+                    top2 = np.sort(col)[-2:]
+                    gap = min(gap, float((top2[1] - top2[0]) / top2[1]))
+                ipiv[j] = p + 1
+                if W[p, j] != 0.0:
+                    if p != j:
+                        W[[j, p], :] = W[[p, j], :]
+                    W[j + 1:, j] = to_fp32(W[j + 1:, j] / W[j, j])
+                elif info == 0:
+                    info = j + 1
+                if j + 1 < k1:
+                    W[j + 1:, j + 1:k1] = to_fp32(W[j + 1:, j + 1:k1]
+                                                 - np.outer(W[j + 1:, j], W[j, j + 1:k1]))
+            if k1 >= E:
+                continue
+            # 2. U12 = L11^{-1} W12 for the super-block's columns right of the
+            #    block, forward substitution with unit diagonal
+            for j in range(k0, k1):
+                if j + 1 < k1:
+                    W[j + 1:k1, k1:E] = to_fp32(W[j + 1:k1, k1:E] - np.outer(W[j + 1:k1, j], W[j, k1:E]))
+            # 3. update of those columns, all rows below the block, in the update precision
+            D = lowprec_product(W[k1:, k0:k1], W[k0:k1, k1:E], prec)
+            W[k1:, k1:E] = (W[k1:, k1:E].astype(np.float32) - D.astype(np.float32)).astype(np.float64)
+        if E >= n:
             break
-        # 2. U12 = L11^{-1} W12, forward substitution with unit diagonal
-        for j in range(k0, k1):
-            if j + 1 < k1:
-                W[j + 1:k1, k1:] = to_fp32(W[j + 1:k1, k1:] - np.outer(W[j + 1:k1, j], W[j, k1:]))
-        # 3. trailing update in the update precision
-        D = lowprec_product(W[k1:, k0:k1], W[k0:k1, k1:], prec)
-        W[k1:, k1:] = (W[k1:, k1:].astype(np.float32) - D.astype(np.float32)).astype(np.float64)
+        # 4. the super-block's rows of the columns right of it, block by block
+        for k0 in range(K0, E, nb):
+            k1 = min(k0 + nb, E)
+            for j in range(k0, k1):
+                if j + 1 < k1:
+                    W[j + 1:k1, E:] = to_fp32(W[j + 1:k1, E:] - np.outer(W[j + 1:k1, j], W[j, E:]))
+            if k1 < E:
+                D = lowprec_product(W[k1:E, k0:k1], W[k0:k1, E:], prec)
+                W[k1:E, E:] = (W[k1:E, E:].astype(np.float32) - D.astype(np.float32)).astype(np.float64)
+        # 5. one rank-(E - K0) update of the rows below the super-block
+        D = lowprec_product(W[E:, K0:E], W[K0:E, E:], prec)
+        W[E:, E:] = (W[E:, E:].astype(np.float32) - D.astype(np.float32)).astype(np.float64)
     if force_ipiv is not None:
         return W, ipiv, info, slack
     if with_gap:

@@ -106,6 +106,42 @@ def test_lowprec_lu_dyadic_exact(prec, n, nb):
     assert np.array_equal(oracle.perm_from_ipiv(ipiv, n), perm.numpy())
 
 
+@pytest.mark.parametrize("prec", ["tf32", "bf16", "fp16", "fp16x3", "bf16x3"])
+@pytest.mark.parametrize("n,nb,ko", [(37, 8, 16), (150, 16, 64), (200, 32, 96)])
+def test_lowprec_lu_two_level_dyadic_exact(prec, n, nb, ko):
+    """Two-level delayed updating (super-blocks of ko columns, ragged last
+    ones) reaches the same exact dyadic factors: every intermediate is a short
+    dyadic rational, so any misplaced block, range or operand order shows."""
+    A, L0, U0, perm = inputs.dyadic_lu(n, seed=510 + n)
+    W, ipiv, info = M.lu_lowprec(A.numpy(), nb, prec, ko=ko)
+    L, U = oracle.unpack_lu(W)
+    assert info == 0
+    assert np.array_equal(L, L0.numpy()) and np.array_equal(U, U0.numpy())
+    assert np.array_equal(oracle.perm_from_ipiv(ipiv, n), perm.numpy())
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16x3", "bf16"])
+def test_lowprec_lu_two_level_reduces_to_one_level(prec):
+    """ko = nb is the one-level algorithm, bit for bit; a larger ko gives a
+    factorisation of the same quality: ||PA - LU|| within the one-level bound,
+    and the same pivots where the update is accurate enough that no near-tie
+    of this input flips (fp32, fp16x3; bf16's 2^-8 rounding does flip some)."""
+    n, nb = 300, 32
+    A = inputs.uniform(n, seed=301).numpy()
+    W1, p1, _ = M.lu_lowprec(A, nb, prec)
+    W2, p2, _ = M.lu_lowprec(A, nb, prec, ko=nb)
+    assert np.array_equal(W1, W2) and np.array_equal(p1, p2)
+    W4, p4, _ = M.lu_lowprec(A, nb, prec, ko=4 * nb)
+    if prec != "bf16":
+        assert np.array_equal(p1, p4)
+    u = {"fp32": 2.0 ** -24, "fp16x3": 2.0 ** -21, "bf16": 2.0 ** -8}[prec]
+    L, U = oracle.unpack_lu(W4)
+    pr = oracle.perm_from_ipiv(p4, n)
+    assert np.abs(A[pr] - L @ U).max() <= 8 * np.sqrt(n) * u * (np.abs(L) @ np.abs(U)).max()
+    with pytest.raises(ValueError):
+        M.lu_lowprec(A, nb, prec, ko=nb + 1)
+
+
 def test_lowprec_lu_fp32_close_to_fp64():
     n = 128
     A = inputs.uniform(n, seed=0).numpy()
