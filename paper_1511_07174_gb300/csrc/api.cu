@@ -549,7 +549,7 @@ size_t gbla_lu_solve_workspace(int n, int nrhs) {
   Carver c(nullptr, 0);
   c.take<int>((size_t)std::max(n, 1));
   c.take<double>((size_t)std::max(n, 1) * std::max(nrhs, 1));
-  c.take<unsigned>(trsv_flags_count(std::max(n, 1)));
+  c.take<unsigned>(trsv_flags_count(std::max(n, 1), std::max(nrhs, 1)));
   return c.off;
 }
 
@@ -570,7 +570,7 @@ int gbla_lu_solve(int trans, int n, int nrhs, const double* LU, int lda, const i
   Carver c(d_work, work_bytes);
   int* perm = c.take<int>((size_t)std::max(n, 1));
   double* T = c.take<double>((size_t)std::max(n, 1) * std::max(nrhs, 1));
-  unsigned* flags = c.take<unsigned>(trsv_flags_count(std::max(n, 1)));
+  unsigned* flags = c.take<unsigned>(trsv_flags_count(std::max(n, 1), std::max(nrhs, 1)));
   if (!c.ok) return GBLA_ERR_WORKSPACE;
   GBLA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), s));
   if (n == 0 || nrhs == 0) return GBLA_OK;
@@ -609,7 +609,7 @@ int gbla_chol_factor(int n, double* A, int lda, int* d_info, int nb, gbla_stream
 size_t gbla_chol_solve_workspace(int n, int nrhs) {
   if (n < 0 || nrhs < 0) return 0;
   Carver c(nullptr, 0);
-  c.take<unsigned>(trsv_flags_count(std::max(n, 1)));
+  c.take<unsigned>(trsv_flags_count(std::max(n, 1), std::max(nrhs, 1)));
   return c.off;
 }
 
@@ -626,7 +626,7 @@ int gbla_chol_solve(int n, int nrhs, const double* L, int lda, double* B, int ld
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (!d_work || !aligned256(d_work)) return GBLA_ERR_WORKSPACE;
   Carver c(d_work, work_bytes);
-  unsigned* flags = c.take<unsigned>(trsv_flags_count(std::max(n, 1)));
+  unsigned* flags = c.take<unsigned>(trsv_flags_count(std::max(n, 1), std::max(nrhs, 1)));
   if (!c.ok) return GBLA_ERR_WORKSPACE;
   GBLA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), s));
   if (n == 0 || nrhs == 0) return GBLA_OK;
@@ -902,7 +902,7 @@ static size_t ir_layout(Carver& c, int n, int m, IrWork* w) {
   t.st = c.take<double>(2);
   t.slots = c.take<double>(mgs_slots_doubles());
   t.counter = c.take<unsigned>(1);
-  t.flags = c.take<unsigned>(trsv_flags_count(nn));
+  t.flags = c.take<unsigned>(trsv_flags_count(nn, 1));
   t.t1 = c.take<double>(nn);
   t.t2 = c.take<double>(nn);
   t.DinvL = c.take<double>(diag_inv_doubles(nn));

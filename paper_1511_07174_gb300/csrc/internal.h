@@ -183,7 +183,7 @@ cudaError_t launch_gemm_tc(int kind, int M, int N, int K, const void* Ak, int ld
 template <typename Ts>
 cudaError_t launch_trsv(bool lower, bool trans, bool unit, int n, int nrhs, const Ts* T, int ldt,
                         double* X, int ldx, unsigned* flags, int* info, cudaStream_t s);
-size_t trsv_flags_count(int n);
+size_t trsv_flags_count(int n, int nrhs);
 
 // Preconditioner apply with inverted 64 x 64 diagonal blocks (one RHS).
 // Dinv holds diag_inv_doubles(n) doubles per triangular factor.

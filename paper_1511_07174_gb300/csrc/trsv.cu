@@ -18,12 +18,24 @@ namespace gbla {
 constexpr int kTsBS = 64;
 constexpr int kTsNR = 16;
 
-size_t trsv_flags_count(int n) { return (size_t)((n + kTsBS - 1) / kTsBS) + 1; }
+// Right-hand sides are split over independent chains of at most kTsPerChain
+// columns each (the columns of X are solved independently), each chain with
+// its own flags: the FP64 work of a chain step shrinks with the columns it
+// carries. At most kTsChains chains per launch.
+constexpr int kTsChains = 16;
+constexpr int kTsPerChain = 4;
+static int trsv_chains(int nrhs) {
+  const int c = (nrhs + kTsPerChain - 1) / kTsPerChain;
+  return c < 1 ? 1 : (c < kTsChains ? c : kTsChains);
+}
+size_t trsv_flags_count(int n, int nrhs) {
+  return (size_t)trsv_chains(nrhs) * (size_t)((n + kTsBS - 1) / kTsBS) + 1;
+}
 
 template <typename Ts, bool LOWER, bool TRANS, bool UNIT>
 __global__ void __launch_bounds__(256)
-    trsv_chain_kernel(int n, int nrhs, const Ts* __restrict__ T, int ldt, double* X, int ldx,
-                      unsigned* flags, int* info, uint64_t wait_ns) {
+    trsv_chain_kernel(int n, int ncols, int G, int C, const Ts* __restrict__ T, int ldt, double* X,
+                      int ldx, unsigned* flags, int* info, uint64_t wait_ns) {
   constexpr bool FWD = (LOWER != TRANS);
   __shared__ double tile[kTsBS][kTsBS + 1];
   __shared__ double xq[kTsBS][kTsNR];
@@ -31,12 +43,19 @@ __global__ void __launch_bounds__(256)
   const int tid = threadIdx.x;
   const int nblk = (n + kTsBS - 1) / kTsBS;
   if (tid == 0) {
-    s_t = (int)atomicAdd(&flags[nblk], 1u);
+    s_t = (int)atomicAdd(&flags[(size_t)C * nblk], 1u);
     s_abort = 0;
   }
   __syncthreads();
-  const int t_ord = s_t;
+  // ticket -> (chain, position in that chain's solve order): a CTA waits only
+  // for earlier positions of its own chain, which hold smaller tickets
+  const int chain = s_t % C;
+  const int t_ord = s_t / C;
   if (t_ord >= nblk) return;
+  flags += (size_t)chain * nblk;
+  X += (size_t)chain * G * ldx;
+  const int nrhs = min(G, ncols - chain * G);
+  if (nrhs <= 0) return;
   const int b = FWD ? t_ord : nblk - 1 - t_ord;
   const int r0 = b * kTsBS;
   const int nr = min(kTsBS, n - r0);
@@ -159,14 +178,19 @@ cudaError_t launch_trsv(bool lower, bool trans, bool unit, int n, int nrhs, cons
   if (n <= 0 || nrhs <= 0) return cudaSuccess;
   const int nblk = (n + kTsBS - 1) / kTsBS;
   const uint64_t wait_ns = wait_timeout_ns();
-  for (int c0 = 0; c0 < nrhs; c0 += kTsNR) {
-    const int nc = nrhs - c0 < kTsNR ? nrhs - c0 : kTsNR;
-    cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(unsigned) * (size_t)(nblk + 1), s);
+  // one launch per kTsChains x kTsNR columns, split over C chains of G columns
+  const int C = trsv_chains(nrhs);
+  for (int c0 = 0; c0 < nrhs; c0 += C * kTsNR) {
+    const int ncols = nrhs - c0 < C * kTsNR ? nrhs - c0 : C * kTsNR;
+    const int G = (ncols + C - 1) / C;
+    const int Cl = (ncols + G - 1) / G;  // chains that hold columns
+    cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(unsigned) * ((size_t)C * nblk + 1), s);
     if (e != cudaSuccess) return e;
     double* Xc = X + (size_t)c0 * ldx;
+    const int grid = Cl * nblk;
 #define GBLA_TRSV(LW, TR, UN)                                                                  \
-  trsv_chain_kernel<Ts, LW, TR, UN><<<nblk, 256, 0, s>>>(n, nc, T, ldt, Xc, ldx, flags, info, \
-                                                         wait_ns)
+  trsv_chain_kernel<Ts, LW, TR, UN><<<grid, 256, 0, s>>>(n, ncols, G, Cl, T, ldt, Xc, ldx, flags, \
+                                                         info, wait_ns)
     if (lower && !trans && unit) GBLA_TRSV(true, false, true);
     else if (lower && !trans && !unit) GBLA_TRSV(true, false, false);
     else if (lower && trans && unit) GBLA_TRSV(true, true, true);
