@@ -18,16 +18,13 @@ namespace gbla {
 constexpr int kTsBS = 64;
 constexpr int kTsNR = 16;
 
-// Right-hand sides are split over independent chains of at most kTsPerChain
-// columns each (the columns of X are solved independently), each chain with
-// its own flags: the FP64 work of a chain step shrinks with the columns it
-// carries. At most kTsChains chains per launch.
-constexpr int kTsChains = 16;
-constexpr int kTsPerChain = 4;
-static int trsv_chains(int nrhs) {
-  const int c = (nrhs + kTsPerChain - 1) / kTsPerChain;
-  return c < 1 ? 1 : (c < kTsChains ? c : kTsChains);
-}
+// Right-hand sides are split over two independent chains (the columns of X
+// are solved independently), each with its own flags: the FP64 work of a
+// chain step halves, and two chains share the SMs without crowding them
+// (measured: 16 columns as 2 x 8 beat 4 x 4 and 8 x 2; 8 columns as 2 x 4
+// beat 1 x 8).
+constexpr int kTsChains = 2;
+static int trsv_chains(int nrhs) { return nrhs < 2 ? 1 : kTsChains; }
 size_t trsv_flags_count(int n, int nrhs) {
   return (size_t)trsv_chains(nrhs) * (size_t)((n + kTsBS - 1) / kTsBS) + 1;
 }
